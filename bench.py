@@ -1,0 +1,328 @@
+"""Stout-smearing benchmark: link-updates/s on one GB300, FP32 (FP64
+Cayley-Hamilton coefficients and re-projection) beside FP64.
+
+Workload: 48^3 x 96 periodic lattice (10,616,832 sites), links exp(i 0.3 H)
+with H random traceless Hermitian (seeded), 6 stout steps rho = 0.125 in all
+4 directions followed by the FP64-accumulated plaquette.  One bench step =
+that whole sequence on device-resident links (each step smears the previous
+step's output in place; the arithmetic per link does not depend on the
+values).  The 3 GB (FP32) / 6 GB (FP64) link fields are far larger than the
+129 MB L2, so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank smears
+its own independent lattice (weak scaling, no data-path collective).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (48, 48, 48, 96)
+N_SMEAR = 6
+RHO = 0.125
+DIRS = (0, 1, 2, 3)
+SEED = 2
+WORKLOAD = "48^3x96 periodic, exp(i*0.3*H) links seed 2, 6 stout steps rho=0.125 in 4 dirs + plaquette"
+METRIC = "stout link-updates/s"
+
+# Algorithmic counts per link update (4 smeared directions), derived in the design doc:
+# minimum traffic = read every link once + write every updated link once.
+BYTES_PER_LINK = {"f32": 144.0, "f64": 288.0}
+
+
+def peaks():
+    p = {}
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    return p
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def time_oracle_sample(n_steps=1, dims=(16, 16, 16, 32)):
+    """Times the FP64 oracle on a bounded sample of the workload (same rho, dirs, generator)."""
+    import fieldgen
+    from oracle import stout
+    U = fieldgen.near_identity_su3(dims, SEED)
+    t0 = time.perf_counter()
+    stout.stout_smear(U, RHO, n_steps, DIRS)
+    dt = time.perf_counter() - t0
+    links = n_steps * int(np.prod(dims)) * len(DIRS)
+    return links / dt, dt, links
+
+
+def run_reference(args, rank):
+    """The oracle as the reference arm: each step a bounded sample (one stout step on 12^3 x 24)."""
+    if rank != 0:
+        return
+    import fieldgen
+    from oracle import gauge, stout
+    dims = (12, 12, 12, 24)
+    U = fieldgen.near_identity_su3(dims, SEED)
+    for _ in range(args.warmup):
+        stout.stout_step(U, RHO, DIRS)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        V1 = stout.stout_step(U, RHO, DIRS)
+        gauge.plaquette(V1)
+        times.append(time.perf_counter() - t0)
+    links = int(np.prod(dims)) * len(DIRS)
+    val = links / float(np.mean(times))
+    sample = f"1 stout step + plaquette on 12^3x24 (same generator, rho, dirs) per bench step, numpy FP64"
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": "link-updates/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "12^3x24"},
+           "cpu_baseline": {"value": val, "unit": "link-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "link-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--f64-steps", type=int, default=3)
+    ap.add_argument("--dims", default=None, help="Lx,Ly,Lz,Lt override (smaller profiling cases)")
+    args = ap.parse_args()
+    global DIMS, WORKLOAD
+    if args.dims:
+        DIMS = tuple(int(x) for x in args.dims.split(","))
+        WORKLOAD = WORKLOAD.replace("48^3x96", "x".join(map(str, DIMS)))
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import fieldgen
+    import paper_1105_2279_gb300 as lq
+    from oracle import lattice, stout
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    V = int(np.prod(DIMS))
+    links_per_step = N_SMEAR * V * len(DIRS)
+    g = lq.Geometry(DIMS)
+
+    # inputs: generated on the device (seed + rank), staged once through the host AoS layout
+    Ut = fieldgen.near_identity_su3_torch(DIMS, SEED + rank, device="cuda")
+    U_host = Ut.cpu().numpy()
+    del Ut
+    torch.cuda.empty_cache()
+    f32 = lq.Field(g, lq.LQ_LINKS, lq.LQ_F32)
+    f64 = lq.Field(g, lq.LQ_LINKS, lq.LQ_F64)
+
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def timed(field, steps, warmup):
+        field.upload(U_host)
+        for _ in range(warmup):
+            lq.stout_smear(field, RHO, N_SMEAR, DIRS)
+            lq.plaquette(field)
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for e0, e1, e2 in ev:
+            e0.record(stream)
+            lq.stout_smear(field, RHO, N_SMEAR, DIRS)   # N_SMEAR launches of the fused step kernel
+            e1.record(stream)
+            lq.plaquette(field)                          # 2 launches, synchronises
+            e2.record(stream)
+        t_all1.record(stream)
+        barrier()
+        total_ms = t_all0.elapsed_time(t_all1)
+        smear_ms = [a.elapsed_time(b) for a, b, _ in ev]
+        step_ms = total_ms / steps
+        if dist is not None:
+            t = torch.tensor([step_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            step_ms = float(t.item())
+        return step_ms, float(np.mean(smear_ms)) / N_SMEAR
+
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+
+    with ClockSampler(local) as clk:
+        step32, kern32 = timed(f32, args.steps, args.warmup)
+        step64, kern64 = timed(f64, args.f64_steps, 1)
+    clocks = clk.summary()
+
+    # accuracy at the stated precision: fresh inputs, one 6-step smearing each
+    f32.upload(U_host)
+    f64.upload(U_host)
+    lq.stout_smear(f32, RHO, N_SMEAR, DIRS)
+    lq.stout_smear(f64, RHO, N_SMEAR, DIRS)
+    p32, p64 = lq.plaquette(f32), lq.plaquette(f64)
+    d32 = f32.download()
+    d64 = f64.download()
+    err_32_64 = float(np.max(np.abs(d32.astype(np.complex128) - d64)))
+    rng = np.random.default_rng(7)
+    e32o, e64o = 0.0, 0.0
+    if rank == 0:
+        for _ in range(3):
+            c = [int(rng.integers(L)) for L in DIMS]
+            ref = stout.stout_smear(lattice.sub_box(U_host, c, N_SMEAR), RHO, N_SMEAR, DIRS)[
+                N_SMEAR, N_SMEAR, N_SMEAR, N_SMEAR]
+            e32o = max(e32o, float(np.max(np.abs(d32[c[3], c[2], c[1], c[0]] - ref))))
+            e64o = max(e64o, float(np.max(np.abs(d64[c[3], c[2], c[1], c[0]] - ref))))
+    del d32, d64
+
+    # end to end through the C ABI with host buffers (pinned): upload, smear, plaquette, download
+    pin_in = torch.from_numpy(U_host.astype(np.complex64).view(np.float32)).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(1):
+        f32.upload_ptr(pin_in.data_ptr())
+        lq.stout_smear(f32, RHO, N_SMEAR, DIRS)
+        lq.plaquette(f32)
+        f32.download_ptr(pin_out.data_ptr())
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        f32.upload_ptr(pin_in.data_ptr())
+        lq.stout_smear(f32, RHO, N_SMEAR, DIRS)
+        lq.plaquette(f32)
+        f32.download_ptr(pin_out.data_ptr())
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, n = time_oracle_sample()
+        cpu = {"value": v, "unit": "link-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"1 FP64 stout step, 4 dirs, on 16^3x32 (same generator and rho): {n} link updates in {dt:.1f} s"}
+
+    if rank == 0:
+        value = world * links_per_step / (step32 * 1e-3)
+        value64 = world * links_per_step / (step64 * 1e-3)
+        links_per_launch = V * len(DIRS)
+        ach32 = BYTES_PER_LINK["f32"] * links_per_launch / (kern32 * 1e-3) / 1e9
+        ach64 = BYTES_PER_LINK["f64"] * links_per_launch / (kern64 * 1e-3) / 1e9
+        out = {
+            "metric": METRIC, "value": value, "unit": "link-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step32, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "precision": "FP32 matrix algebra and storage; FP64 Cayley-Hamilton coefficients, SU(3) re-projection and plaquette accumulation",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "n_smear": N_SMEAR, "rho": RHO, "dirs": "xyzt",
+                       "l2": "inputs larger than L2 (3.06 GB FP32 links)", "per_rank": "independent lattice per rank"},
+            "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
+                         "traffic": None, "kernel": "k_stout_global<float,reproject>",
+                         "kernel_ms": kern32, "peak_source": "measured hbm_gbs"},
+            "fp64": {"value": value64, "ms_per_step": step64, "kernel_ms": kern64,
+                     "roofline": {"bound": "hbm", "achieved": ach64, "peak": hbm, "unit": "GB/s", "frac": ach64 / hbm}},
+            "fp32_speedup_vs_fp64": value / value64,
+            "accuracy": {"fp32_vs_fp64_gpu_max_abs": err_32_64, "fp32_vs_oracle_sampled_max_abs": e32o,
+                         "fp64_vs_oracle_sampled_max_abs": e64o, "plaquette_fp32": p32[0], "plaquette_fp64": p64[0],
+                         "plaquette_abs_diff": abs(p32[0] - p64[0])},
+            "e2e": {"value": world * links_per_step / (e2e_ms * 1e-3), "unit": "link-updates/s",
+                    "h2d_bytes_per_step": int(pin_in.numel() * 4), "d2h_bytes_per_step": int(pin_out.numel() * 4),
+                    "ms_per_step": e2e_ms},
+            "gpu_launches": args.steps * (N_SMEAR + 2),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

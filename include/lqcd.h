@@ -1,0 +1,247 @@
+/*
+ * lqcd.h -- C ABI of liblqcd, a GB300 (sm_103a) library for site-wise lattice
+ * field expressions and stout link smearing on a periodic 4D lattice.
+ *
+ * Sources of the operations (cited per entry point below):
+ *   [W]   F. Winter, "Accelerating QDP++ using GPUs" (arXiv:1105.2279):
+ *         Sec. 4.2 (flattened expression evaluation, shift site tables),
+ *         Sec. 4.4 (thread geometry N_threads / N_site, auto-tuning),
+ *         Sec. 5 (device residency API), Sec. 6 Listing 1 (shift, adj,
+ *         products, the Jacobi smearing routine), Sec. 8 (coalesced layout,
+ *         auto-tuning as next steps).
+ *   [MP]  C. Morningstar, M. Peardon, Phys. Rev. D 69 (2004) 054501:
+ *         Sec. II (stout link), Sec. III (Cayley-Hamilton exp(iQ)),
+ *         Sec. IV (stout force recursion).
+ *
+ * Conventions shared by every call
+ *   - Lattice dims (Lx, Ly, Lz, Lt); mu = 0,1,2,3 = x,y,z,t; site index
+ *     s = x + Lx*(y + Ly*(z + Lz*t)); periodic in every direction.
+ *     A link U_mu(x) sits on the bond x -> x + mu.
+ *   - Device layout (structure of arrays, component-major): an element is a
+ *     complex number stored as (re, im) = float2 / double2, except kind
+ *     LQ_REAL (one float / double).  A field of kind k holds
+ *     [ndir][ncomp][V] elements with (ndir, ncomp) = LINKS (4, 9),
+ *     COLOR_MATRIX (1, 9), COLOR_VECTOR (1, 3), COMPLEX (1, 1), REAL (1, 1);
+ *     matrix component c = 3*row + col.  Consecutive threads read
+ *     consecutive sites of one component plane (coalesced 8/16 B vectors).
+ *   - Host interchange layout (AoS, the QDP++ site-major order):
+ *     [V][ndir][ncomp] elements of the field's precision, (re, im)
+ *     interleaved.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on it, except those that return host values
+ *     (reductions, plaquette, upload/download), which synchronise it.
+ *   - Every call returns an lq_status; on error nothing is launched, output
+ *     fields are left untouched and lq_last_error() describes the failure.
+ *     No call aborts, traps or prints.
+ *   - Ownership: handles (lq_geom, lq_field) belong to the caller and are
+ *     released with the matching destroy/free call; memory passed to
+ *     lq_field_wrap stays owned by the caller; host buffers are never kept.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int lq_status;
+#define LQ_OK                0
+#define LQ_ERR_ARG          (-1)  /* invalid argument (NULL, range, aliasing)           */
+#define LQ_ERR_GEOM         (-2)  /* fields on different geometries / wrong kind        */
+#define LQ_ERR_OOM          (-3)  /* device allocation failed                           */
+#define LQ_ERR_CUDA         (-4)  /* a CUDA runtime call failed                         */
+#define LQ_ERR_TIMEOUT      (-5)  /* a bounded device-side wait gave up                 */
+#define LQ_ERR_NUMERIC      (-6)  /* non-finite value detected where checked            */
+#define LQ_ERR_UNSUPPORTED  (-7)  /* valid request this build does not implement        */
+
+typedef enum lq_kind {
+  LQ_LINKS = 0, LQ_COLOR_MATRIX = 1, LQ_COLOR_VECTOR = 2, LQ_COMPLEX = 3, LQ_REAL = 4
+} lq_kind;
+
+typedef enum lq_prec { LQ_F32 = 0, LQ_F64 = 1 } lq_prec;
+
+typedef struct lq_geom lq_geom;    /* opaque: lattice dims and volume        */
+typedef struct lq_field lq_field;  /* opaque: geometry, kind, prec, device ptr */
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char* lq_last_error(void);
+
+/* ABI version of this header (1). */
+int lq_abi_version(void);
+
+/* ---- geometry and fields ([W] Sec. 5; layout [W] Sec. 8) -------------- */
+
+/* dims: 4 ints >= 1 with Lx*Ly*Lz*Lt < 2^31.  *out receives a new handle. */
+lq_status lq_geom_create(const int dims[4], lq_geom** out);
+lq_status lq_geom_destroy(lq_geom* g);
+/* Volume V and dims of a geometry. */
+lq_status lq_geom_info(const lq_geom* g, int dims_out[4], long long* volume_out);
+
+/* Bytes of a field of (kind, prec) on g: V * ndir * ncomp * element size. */
+lq_status lq_field_bytes(const lq_geom* g, int kind, int prec, size_t* bytes_out);
+
+/* Allocates a device field owned by the library (stream-ordered on `stream`,
+ * contents undefined); release with lq_field_free.  Counterpart of the
+ * paper's pushToLattice() allocation ([W] Sec. 5). */
+lq_status lq_field_alloc(const lq_geom* g, int kind, int prec, void* stream, lq_field** out);
+
+/* Wraps caller-owned device memory (e.g. a torch tensor) as a field.
+ * dev_ptr must be 16-byte aligned and hold at least lq_field_bytes(). */
+lq_status lq_field_wrap(const lq_geom* g, int kind, int prec, void* dev_ptr, size_t bytes,
+                        lq_field** out);
+
+/* Releases the handle; frees the memory only if the library allocated it
+ * (freeDeviceMem(), [W] Sec. 5). */
+lq_status lq_field_free(lq_field* f);
+
+/* Device pointer of a field (structure-of-arrays layout above). */
+lq_status lq_field_device_ptr(const lq_field* f, void** ptr_out);
+
+/* Host AoS -> device SoA ([W] Sec. 5 pushToLattice copy).  host_aos holds
+ * lq_field_bytes() bytes in the host interchange layout; it is read before
+ * the call returns (the stream is synchronised).  Pinned host memory makes
+ * the copy asynchronous-capable and faster. */
+lq_status lq_field_upload(lq_field* f, const void* host_aos, void* stream);
+
+/* Device SoA -> host AoS ([W] Sec. 5 popFromLattice copy); synchronises. */
+lq_status lq_field_download(const lq_field* f, void* host_aos, void* stream);
+
+/* ---- site-wise operations ([W] Sec. 6 Listing 1) ------------------------ */
+
+/* out(x) = in(x + sign*mu), periodic: sign = +1 is QDP++ FORWARD, -1
+ * BACKWARD (Listing 1).  out and in: same geometry, kind and precision,
+ * distinct memory.  No site table is read: neighbours are index arithmetic. */
+lq_status lq_shift(lq_field* out, const lq_field* in, int mu, int sign, void* stream);
+
+/* Flattened expression program ([W] Sec. 4.2): a per-site register machine
+ * over 3x3 complex matrices.  A COLOR_VECTOR operand is loaded into column 0
+ * (other columns zero) and stored from column 0; COMPLEX/REAL operands load
+ * as scalar * identity and store the (0,0) entry. */
+enum {
+  LQ_OP_LOAD = 0,   /* r[dst] = shift(operand[a] (dir `dir` if LINKS), sign, mu); sign 0: no shift */
+  LQ_OP_ADJ = 1,    /* r[dst] = r[a]^dagger                                       */
+  LQ_OP_MUL = 2,    /* r[dst] = r[a] * r[b]                                       */
+  LQ_OP_ADD = 3,    /* r[dst] = r[a] + r[b]                                       */
+  LQ_OP_SUB = 4,    /* r[dst] = r[a] - r[b]                                       */
+  LQ_OP_SCALE = 5,  /* r[dst] = (re + i im) * r[a]                                */
+  LQ_OP_TRACE = 6,  /* r[dst] = tr(r[a]) * 1                                      */
+  LQ_OP_RETR = 7,   /* r[dst] = Re tr(r[a]) * 1                                   */
+  LQ_OP_STORE = 8   /* result = r[a]                                              */
+};
+#define LQ_EXPR_MAX_OPS 64
+#define LQ_EXPR_MAX_REGS 8
+#define LQ_EXPR_MAX_OPERANDS 8
+typedef struct lq_op {
+  int code, dst, a, b;   /* opcode and register / operand indices            */
+  int dir, mu, sign;     /* LOAD: link direction, shift direction and sign   */
+  int pad;
+  double re, im;         /* SCALE factor                                      */
+} lq_op;
+
+/* Evaluates `prog` at every site.  operands: n_operands fields of one
+ * geometry and precision.  If out_or_null is given (kind COLOR_MATRIX,
+ * COLOR_VECTOR, COMPLEX or REAL), the stored register is written to it.  If
+ * reduce_out_or_null is given, it receives sum_x tr(result(x)) as
+ * (re, im), accumulated in FP64 in a fixed order (run-to-run bit identical);
+ * the stream is then synchronised.  The program must end with one STORE. */
+lq_status lq_expr_eval(lq_field* out_or_null, const lq_op* prog, int n_ops,
+                       const lq_field* const* operands, int n_operands,
+                       double* reduce_out_or_null, void* stream);
+
+/* ---- global reductions (FP64 accumulation, deterministic) ---------------- */
+
+/* out[0..1] = sum over sites and components (re, im); REAL fields give im = 0. */
+lq_status lq_reduce_sum(const lq_field* f, double out[2], void* stream);
+
+/* out[0..1] = sum_x tr M(x) for COLOR_MATRIX; sum_x sum_mu tr U_mu(x) for LINKS. */
+lq_status lq_reduce_trace(const lq_field* f, double out[2], void* stream);
+
+/* Average plaquette of a LINKS field:
+ *   out[0] = (1/(18V)) sum_x sum_{mu<nu} Re tr P_{mu nu}(x)   (unit field -> 1),
+ *   out[1] = spatial planes (nu < 3), out[2] = temporal planes, each / (9V),
+ * with P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag.
+ * Products in the field precision, accumulation in FP64.  Synchronises. */
+lq_status lq_plaquette(const lq_field* links, double out[3], void* stream);
+
+/* Wilson action S = beta sum_x sum_{mu<nu} (1 - Re tr P_{mu nu}(x)/3). */
+lq_status lq_wilson_action(const lq_field* links, double beta, double* out, void* stream);
+
+/* ---- stout smearing ([MP] Secs. II-IV) ------------------------------------ */
+
+typedef struct lq_stout_opts {
+  int struct_size;        /* sizeof(lq_stout_opts); 0 => all defaults               */
+  int reproject;          /* -1 default (on for LQ_F32 links, off for LQ_F64), 0, 1 */
+  int use_graph;          /* 1: record the n-step launch sequence as a CUDA graph
+                             and replay it (cached per field, dims, n, rho, dirs)   */
+  int variant;            /* 0 tuned/default, 1 global-load kernel,
+                             2 shared-memory staged kernel                           */
+  int block;              /* threads per block (N_threads, [W] Sec. 4.4); 0 = tuned  */
+  int sites_per_thread;   /* N_site ([W] Sec. 4.4); 0 = tuned                        */
+  void* work;             /* optional device workspace of >= one links field;
+                             NULL => the library allocates it stream-ordered         */
+  size_t work_bytes;
+} lq_stout_opts;
+
+/* n_steps stout steps in place on a LINKS field.  dirs_mask bit mu selects
+ * smeared directions; staples sum over nu in dirs, nu != mu; links outside
+ * dirs are unchanged.  Each step computes every new link from the previous
+ * step's field (double-buffered internally).  Precision follows the field:
+ *   LQ_F64: all arithmetic FP64.
+ *   LQ_F32: staples, Omega, Q, exp assembly and U' = exp(iQ) U in FP32;
+ *           Cayley-Hamilton coefficients f0,f1,f2 in FP64; SU(3)
+ *           re-projection of every new link in FP64 (unless reproject = 0).
+ * rho >= 0 and finite; n_steps >= 0; dirs_mask in [1, 15]. */
+lq_status lq_stout_smear(lq_field* links_inout, double rho, int n_steps, unsigned dirs_mask,
+                         const lq_stout_opts* opts, void* stream);
+
+typedef struct lq_backward_opts {
+  int struct_size;        /* sizeof(lq_backward_opts); 0 => defaults                */
+  int checkpoint_every;   /* k >= 1: keep U^(j) for j % k == 0 and recompute the
+                             others forward from the nearest kept field; 1 (default)
+                             keeps every step                                        */
+} lq_backward_opts;
+
+/* Gradient of a scalar S(stout^n(U)) with respect to the thin links U.
+ *   grad_seed: LINKS field G_n = dS/dRe U^(n) + i dS/dIm U^(n); NULL =>
+ *              S is the Wilson action of the smeared field at `beta`.
+ *   force_out: LINKS field receiving F_mu(x) = TA(G_mu(x) U_mu(x)^dag)
+ *              (traceless anti-Hermitian; d/de S(exp(eX)U_mu(x)) = Re tr F^dag X).
+ *   grad_out:  optional LINKS field receiving G w.r.t. the thin links.
+ * The recursion is the stout force of [MP] Sec. IV, evaluated with the same
+ * precision rules as lq_stout_smear (FP32 links: FP32 matrix algebra, FP64
+ * coefficients).  Scratch memory (checkpoints and two gradient fields) is
+ * allocated stream-ordered. */
+lq_status lq_stout_backward(const lq_field* thin_links, double rho, int n_steps, unsigned dirs_mask,
+                            const lq_field* grad_seed, double beta, lq_field* force_out,
+                            lq_field* grad_out, const lq_backward_opts* opts, void* stream);
+
+/* Smears n_cfg independent LINKS fields (any geometries, one precision) with
+ * one persistent launch per step over a device work list of (config, tile)
+ * items; with opts->use_graph the n-step sequence is a replayed CUDA graph.
+ * Results equal n_cfg separate lq_stout_smear calls bit for bit. */
+lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, int n_steps,
+                               unsigned dirs_mask, const lq_stout_opts* opts, void* stream);
+
+/* ---- auto-tuning ([W] Sec. 4.4 and Sec. 8) and device storage ------------- */
+
+/* Enables the auto-tuner: the first smearing call per (kernel, precision,
+ * dims, device) times the candidate block sizes and N_site values on a
+ * scratch copy and keeps the fastest.  cache_path (may be NULL) names a
+ * text file that is read now and rewritten after each new entry. */
+lq_status lq_tune(const char* cache_path);
+
+/* The tuned (block, sites_per_thread, variant) for a key, if known. */
+lq_status lq_tune_lookup(int prec, const int dims[4], unsigned dirs_mask, int* block,
+                         int* sites_per_thread, int* variant);
+
+/* Releases every cache the library holds on the device (workspaces, graphs,
+ * descriptor tables), like theDeviceStorage::freeAll() ([W] Sec. 5).
+ * Fields are not touched. */
+lq_status lq_free_all(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */

@@ -1,0 +1,269 @@
+"""Python binding of liblqcd, the GB300 (sm_103a) library for lattice field
+expressions and stout link smearing.
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels, reached through the C ABI of include/lqcd.h via
+ctypes.  PyTorch supplies device memory (fields are torch tensors in the
+structure-of-arrays layout [ndir, ncomp, V, 2]) and the current CUDA stream.
+The functions carry the C names without the ``lq_`` prefix; the raw C
+entry points are available as ``paper_1105_2279_gb300.capi()``.
+"""
+import ctypes
+from ctypes import byref, c_double, c_int, c_longlong, c_size_t, c_void_p
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import (LQ_COLOR_MATRIX, LQ_COLOR_VECTOR, LQ_COMPLEX, LQ_F32, LQ_F64, LQ_LINKS,  # noqa: F401
+                   LQ_REAL, LqBackwardOpts, LqOp, LqStoutOpts)
+
+KIND_SHAPE = {LQ_LINKS: (4, 9), LQ_COLOR_MATRIX: (1, 9), LQ_COLOR_VECTOR: (1, 3), LQ_COMPLEX: (1, 1),
+              LQ_REAL: (1, 1)}
+# per-site trailing shape of the host (AoS) arrays
+SITE_SHAPE = {LQ_LINKS: (4, 3, 3), LQ_COLOR_MATRIX: (3, 3), LQ_COLOR_VECTOR: (3,), LQ_COMPLEX: (), LQ_REAL: ()}
+
+
+class LqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+def capi():
+    return L.load()
+
+
+def _check(st, what):
+    if st != L.LQ_OK:
+        msg = L.load().lq_last_error().decode(errors="replace")
+        raise LqError(st, f"{what}: {L.STATUS_NAMES.get(st, st)}: {msg}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return c_void_p(int(stream))
+    import torch
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def dirs_mask(dirs):
+    if isinstance(dirs, int):
+        return dirs
+    m = 0
+    for mu in dirs:
+        m |= 1 << int(mu)
+    return m
+
+
+class Geometry:
+    """Periodic 4D lattice (Lx, Ly, Lz, Lt); site index x fastest."""
+
+    def __init__(self, dims):
+        self.dims = tuple(int(d) for d in dims)
+        arr = (c_int * 4)(*self.dims)
+        h = c_void_p()
+        _check(L.load().lq_geom_create(arr, byref(h)), "lq_geom_create")
+        self.handle = h
+        self.volume = int(np.prod(self.dims))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and L._lib is not None:
+            L._lib.lq_geom_destroy(h)
+            self.handle = None
+
+
+class Field:
+    """A lattice field in device memory: a torch tensor wrapped as an lq_field."""
+
+    def __init__(self, geom, kind, prec, tensor=None, device="cuda"):
+        import torch
+        self.geom, self.kind, self.prec = geom, kind, prec
+        nd, nc = KIND_SHAPE[kind]
+        dt = torch.float64 if prec == LQ_F64 else torch.float32
+        shape = (nd, nc, geom.volume) if kind == LQ_REAL else (nd, nc, geom.volume, 2)
+        if tensor is None:
+            tensor = torch.empty(shape, dtype=dt, device=device)
+        if tuple(tensor.shape) != shape or tensor.dtype != dt or not tensor.is_contiguous():
+            raise ValueError(f"tensor must be contiguous {dt} of shape {shape}")
+        self.tensor = tensor
+        h = c_void_p()
+        _check(L.load().lq_field_wrap(geom.handle, kind, prec, c_void_p(tensor.data_ptr()),
+                                      tensor.numel() * tensor.element_size(), byref(h)), "lq_field_wrap")
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and L._lib is not None:
+            L._lib.lq_field_free(h)
+            self.handle = None
+
+    @property
+    def nbytes(self):
+        return self.tensor.numel() * self.tensor.element_size()
+
+    def host_dtype(self):
+        if self.kind == LQ_REAL:
+            return np.float64 if self.prec == LQ_F64 else np.float32
+        return np.complex128 if self.prec == LQ_F64 else np.complex64
+
+    def host_shape(self):
+        lx, ly, lz, lt = self.geom.dims
+        return (lt, lz, ly, lx) + SITE_SHAPE[self.kind]
+
+    def upload(self, host, stream=None):
+        """host: array in the AoS interchange layout (any shape with the right size); converted to
+        the field precision on the host, then copied and transposed on the device."""
+        a = np.ascontiguousarray(np.asarray(host).astype(self.host_dtype(), copy=False))
+        if a.nbytes != self.nbytes:
+            raise ValueError(f"host array has {a.nbytes} bytes, field needs {self.nbytes}")
+        _check(L.load().lq_field_upload(self.handle, c_void_p(a.ctypes.data), _stream(stream)), "lq_field_upload")
+
+    def upload_ptr(self, host_ptr, stream=None):
+        _check(L.load().lq_field_upload(self.handle, c_void_p(host_ptr), _stream(stream)), "lq_field_upload")
+
+    def download(self, stream=None):
+        a = np.empty(self.host_shape(), dtype=self.host_dtype())
+        _check(L.load().lq_field_download(self.handle, c_void_p(a.ctypes.data), _stream(stream)),
+               "lq_field_download")
+        return a
+
+    def download_ptr(self, host_ptr, stream=None):
+        _check(L.load().lq_field_download(self.handle, c_void_p(host_ptr), _stream(stream)), "lq_field_download")
+
+    @classmethod
+    def from_host(cls, geom, kind, prec, host, device="cuda", stream=None):
+        f = cls(geom, kind, prec, device=device)
+        f.upload(host, stream)
+        return f
+
+
+def shift(out, inp, mu, sign, stream=None):
+    """out(x) = inp(x + sign*mu) (sign +1 FORWARD, -1 BACKWARD)."""
+    _check(L.load().lq_shift(out.handle, inp.handle, int(mu), int(sign), _stream(stream)), "lq_shift")
+
+
+def compile_program(prog):
+    """Tuple program (oracle.expr notation) -> ctypes array of LqOp."""
+    ops = []
+    for op in prog:
+        k = op[0]
+        o = LqOp()
+        if k == "load":
+            o.code, o.dst, o.a, o.mu, o.sign = L.LQ_OP_LOAD, op[1], op[2], op[3], op[4]
+        elif k == "loadl":
+            o.code, o.dst, o.a, o.dir, o.mu, o.sign = L.LQ_OP_LOAD, op[1], op[2], op[3], op[4], op[5]
+        elif k in ("adj", "trace", "retr"):
+            o.code = {"adj": L.LQ_OP_ADJ, "trace": L.LQ_OP_TRACE, "retr": L.LQ_OP_RETR}[k]
+            o.dst, o.a = op[1], op[2]
+        elif k in ("mul", "add", "sub"):
+            o.code = {"mul": L.LQ_OP_MUL, "add": L.LQ_OP_ADD, "sub": L.LQ_OP_SUB}[k]
+            o.dst, o.a, o.b = op[1], op[2], op[3]
+        elif k == "scale":
+            o.code, o.dst, o.a, o.re, o.im = L.LQ_OP_SCALE, op[1], op[2], float(op[3]), float(op[4])
+        elif k == "store":
+            o.code, o.a = L.LQ_OP_STORE, op[1]
+        else:
+            raise ValueError(f"op {k!r} has no C-ABI form (shifts apply to loads)")
+        ops.append(o)
+    arr = (LqOp * len(ops))(*ops)
+    return arr, len(ops)
+
+
+def expr_eval(prog, operands, out=None, reduce=False, stream=None):
+    """Evaluates a per-site program; returns sum_x tr(result) if reduce."""
+    arr, n = compile_program(prog)
+    hs = (c_void_p * len(operands))(*[f.handle for f in operands])
+    red = (c_double * 2)()
+    _check(L.load().lq_expr_eval(out.handle if out is not None else None, arr, n, hs, len(operands),
+                                 red if reduce else None, _stream(stream)), "lq_expr_eval")
+    return complex(red[0], red[1]) if reduce else None
+
+
+def reduce_sum(f, stream=None):
+    r = (c_double * 2)()
+    _check(L.load().lq_reduce_sum(f.handle, r, _stream(stream)), "lq_reduce_sum")
+    return complex(r[0], r[1])
+
+
+def reduce_trace(f, stream=None):
+    r = (c_double * 2)()
+    _check(L.load().lq_reduce_trace(f.handle, r, _stream(stream)), "lq_reduce_trace")
+    return complex(r[0], r[1])
+
+
+def plaquette(links, stream=None):
+    """(average, spatial, temporal) plaquette."""
+    r = (c_double * 3)()
+    _check(L.load().lq_plaquette(links.handle, r, _stream(stream)), "lq_plaquette")
+    return (r[0], r[1], r[2])
+
+
+def wilson_action(links, beta, stream=None):
+    r = c_double()
+    _check(L.load().lq_wilson_action(links.handle, float(beta), byref(r), _stream(stream)), "lq_wilson_action")
+    return r.value
+
+
+def stout_opts(reproject=None, use_graph=False, variant=0, block=0, sites_per_thread=0, work=None):
+    o = LqStoutOpts()
+    o.struct_size = ctypes.sizeof(LqStoutOpts)
+    o.reproject = -1 if reproject is None else int(bool(reproject))
+    o.use_graph = int(bool(use_graph))
+    o.variant, o.block, o.sites_per_thread = int(variant), int(block), int(sites_per_thread)
+    if work is not None:
+        o.work = c_void_p(work.data_ptr())
+        o.work_bytes = work.numel() * work.element_size()
+    return o
+
+
+def stout_smear(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None, **opts):
+    """In-place stout smearing of a LINKS field (see lq_stout_smear)."""
+    o = stout_opts(**opts)
+    _check(L.load().lq_stout_smear(links.handle, float(rho), int(n_steps), dirs_mask(dirs), byref(o),
+                                   _stream(stream)), "lq_stout_smear")
+
+
+def stout_smear_batch(fields, rho, n_steps, dirs=(0, 1, 2), stream=None, **opts):
+    o = stout_opts(**opts)
+    hs = (c_void_p * len(fields))(*[f.handle for f in fields])
+    _check(L.load().lq_stout_smear_batch(hs, len(fields), float(rho), int(n_steps), dirs_mask(dirs), byref(o),
+                                         _stream(stream)), "lq_stout_smear_batch")
+
+
+def stout_backward(thin, rho, n_steps, dirs, force_out, grad_seed=None, beta=6.0, grad_out=None,
+                   checkpoint_every=1, stream=None):
+    o = LqBackwardOpts()
+    o.struct_size = ctypes.sizeof(LqBackwardOpts)
+    o.checkpoint_every = int(checkpoint_every)
+    _check(L.load().lq_stout_backward(thin.handle, float(rho), int(n_steps), dirs_mask(dirs),
+                                      grad_seed.handle if grad_seed is not None else None, float(beta),
+                                      force_out.handle, grad_out.handle if grad_out is not None else None,
+                                      byref(o), _stream(stream)), "lq_stout_backward")
+
+
+def tune(cache_path=None):
+    _check(L.load().lq_tune(cache_path.encode() if cache_path else None), "lq_tune")
+
+
+def tune_lookup(prec, dims, dirs):
+    b, n, v = c_int(), c_int(), c_int()
+    st = L.load().lq_tune_lookup(int(prec), (c_int * 4)(*dims), dirs_mask(dirs), byref(b), byref(n), byref(v))
+    return (b.value, n.value, v.value) if st == L.LQ_OK else None
+
+
+def free_all():
+    _check(L.load().lq_free_all(), "lq_free_all")
+
+
+def field_bytes(geom, kind, prec):
+    n = c_size_t()
+    _check(L.load().lq_field_bytes(geom.handle, kind, prec, byref(n)), "lq_field_bytes")
+    return n.value
+
+
+def geom_info(geom):
+    d = (c_int * 4)()
+    v = c_longlong()
+    _check(L.load().lq_geom_info(geom.handle, d, byref(v)), "lq_geom_info")
+    return tuple(d), v.value

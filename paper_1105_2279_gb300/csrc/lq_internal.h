@@ -1,0 +1,115 @@
+// Internal host-side definitions shared by the liblqcd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/lqcd.h"
+
+struct lq_geom {
+  int dims[4];
+  long long volume;
+};
+
+struct lq_field {
+  lq_geom geom;      // copied, so a field outlives its geometry handle
+  int kind;
+  int prec;
+  void* ptr;
+  size_t bytes;
+  bool owned;
+};
+
+namespace lq {
+
+// Thread-local last error message.
+void set_error(const char* fmt, ...);
+void clear_error();
+
+inline int ndir_of(int kind) { return kind == LQ_LINKS ? 4 : 1; }
+inline int ncomp_of(int kind) {
+  switch (kind) {
+    case LQ_LINKS:
+    case LQ_COLOR_MATRIX: return 9;
+    case LQ_COLOR_VECTOR: return 3;
+    default: return 1;
+  }
+}
+inline size_t elem_bytes(int kind, int prec) {
+  size_t r = prec == LQ_F64 ? 8 : 4;
+  return kind == LQ_REAL ? r : 2 * r;
+}
+inline bool valid_kind(int k) { return k >= LQ_LINKS && k <= LQ_REAL; }
+inline bool valid_prec(int p) { return p == LQ_F32 || p == LQ_F64; }
+inline size_t field_bytes(const lq_geom& g, int kind, int prec) {
+  return (size_t)g.volume * ndir_of(kind) * ncomp_of(kind) * elem_bytes(kind, prec);
+}
+inline bool same_geom(const lq_geom& a, const lq_geom& b) {
+  return a.dims[0] == b.dims[0] && a.dims[1] == b.dims[1] && a.dims[2] == b.dims[2] &&
+         a.dims[3] == b.dims[3];
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Returns LQ_ERR_CUDA (with message) if e != cudaSuccess.
+lq_status cuda_check(cudaError_t e, const char* what);
+// Checks the launch just issued.
+lq_status launch_check(const char* what);
+
+int device_sm_count();
+int current_device();
+
+// Stream-ordered scratch allocation that reports OOM as LQ_ERR_OOM.
+lq_status scratch_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
+void scratch_free(void* p, cudaStream_t s);
+
+// Geometry parameters passed to kernels by value.
+struct GeomArgs {
+  int L[4];
+  int stride[4];   // 1, Lx, Lx*Ly, Lx*Ly*Lz
+  int V;
+};
+inline GeomArgs geom_args(const lq_geom& g) {
+  GeomArgs a;
+  int st = 1;
+  for (int i = 0; i < 4; ++i) {
+    a.L[i] = g.dims[i];
+    a.stride[i] = st;
+    st *= g.dims[i];
+  }
+  a.V = (int)g.volume;
+  return a;
+}
+
+// Validation helpers (set the error message and return the status).
+lq_status check_links(const lq_field* f, const char* who);
+lq_status check_dirs(unsigned mask, const char* who);
+
+// Autotuner (tune.cu).
+struct TuneChoice {
+  int block;
+  int nsite;
+  int variant;
+};
+bool tune_enabled();
+bool tune_get(const char* kernel, int prec, const int dims[4], unsigned dirs, TuneChoice* out);
+void tune_put(const char* kernel, int prec, const int dims[4], unsigned dirs, const TuneChoice& c);
+
+// Stout internals shared with the backward and batch translation units.
+lq_status stout_run_steps(void* links, void* work, const lq_geom& g, int prec, double rho,
+                          int n_steps, unsigned dirs, int reproject, const TuneChoice& tc,
+                          cudaStream_t s);
+TuneChoice stout_default_choice(int prec);
+lq_status stout_choose(const lq_field* f, double rho, unsigned dirs, int reproject,
+                       const lq_stout_opts* o, cudaStream_t s, TuneChoice* out);
+
+// Reductions shared by several entry points.
+lq_status plaquette_sums(const lq_field* links, double out_planes[2], cudaStream_t s);
+
+// Registered cleanup callbacks for lq_free_all.
+void register_cache_release(void (*fn)());
+
+}  // namespace lq

@@ -1,0 +1,301 @@
+// Stout link smearing: one fused kernel per step (staples -> Omega -> Q ->
+// FP64 Cayley-Hamilton coefficients -> exp(iQ) U -> optional FP64
+// re-projection), double-buffered over n steps, optionally replayed as a
+// CUDA graph (Morningstar & Peardon 2004, Secs. II-III; thread geometry
+// N_threads / N_site of Winter, "Accelerating QDP++ using GPUs", Sec. 4.4).
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "lq_internal.h"
+#include "stout_core.cuh"
+
+namespace lq {
+
+struct MuList {
+  int mu[4];
+};
+
+// Variant 1: one thread per (site, mu) for N_site sites; neighbour links are
+// read through the read-only data path (L1 / L2 serve the ~19x reuse of each
+// link by neighbouring staples).
+template <typename R, bool REPRO>
+__global__ void __launch_bounds__(256) k_stout_global(const typename vec2<R>::type* __restrict__ Uin,
+                                                      typename vec2<R>::type* __restrict__ Uout, GeomArgs g,
+                                                      R rho, unsigned dirs, int nsite, MuList ml) {
+  const int mu = ml.mu[blockIdx.y];
+  const long long V = g.V;
+  for (int k = 0; k < nsite; ++k) {
+    const long long sl = ((long long)blockIdx.x * nsite + k) * blockDim.x + threadIdx.x;
+    if (sl >= V) return;
+    const int s = (int)sl;
+    int c[4];
+    site_coords(g, s, c);
+    const M3<R> Up = stout_link<R>(Uin, g, s, c, mu, dirs, rho, REPRO);
+    st_m3<R>(Uout + (long long)mu * 9 * V + s, V, Up);
+  }
+}
+
+static MuList mu_list(unsigned dirs, int* n) {
+  MuList m;
+  int k = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    if ((dirs >> mu) & 1u) m.mu[k++] = mu;
+  for (int j = k; j < 4; ++j) m.mu[j] = 0;
+  *n = k;
+  return m;
+}
+
+static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int prec, double rho,
+                             unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s) {
+  const GeomArgs g = geom_args(geom);
+  int nd = 0;
+  const MuList ml = mu_list(dirs, &nd);
+  const int block = tc.block > 0 ? tc.block : 128;
+  const int nsite = tc.nsite > 0 ? tc.nsite : 1;
+  const long long per_block = (long long)block * nsite;
+  dim3 grid((unsigned)((g.V + per_block - 1) / per_block), (unsigned)nd);
+  if (prec == LQ_F64) {
+    if (reproject)
+      k_stout_global<double, true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, ml);
+    else
+      k_stout_global<double, false><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, ml);
+  } else {
+    if (reproject)
+      k_stout_global<float, true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, ml);
+    else
+      k_stout_global<float, false><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, ml);
+  }
+  return launch_check("stout step kernel");
+}
+
+static size_t dir_block_bytes(const lq_geom& g, int prec) {
+  return (size_t)g.volume * 9 * elem_bytes(LQ_LINKS, prec);
+}
+
+lq_status stout_run_steps(void* links, void* work, const lq_geom& g, int prec, double rho, int n_steps,
+                          unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s) {
+  if (n_steps <= 0) return LQ_OK;
+  const size_t db = dir_block_bytes(g, prec);
+  // links outside `dirs` are never written: give the work buffer a copy once
+  for (int mu = 0; mu < 4; ++mu)
+    if (!((dirs >> mu) & 1u)) {
+      lq_status st = cuda_check(cudaMemcpyAsync((char*)work + mu * db, (const char*)links + mu * db, db,
+                                                cudaMemcpyDeviceToDevice, s),
+                                "stout pass-through copy");
+      if (st != LQ_OK) return st;
+    }
+  for (int k = 0; k < n_steps; ++k) {
+    const void* in = (k % 2 == 0) ? links : work;
+    void* out = (k % 2 == 0) ? work : links;
+    lq_status st = launch_step(in, out, g, prec, rho, dirs, reproject, tc, s);
+    if (st != LQ_OK) return st;
+  }
+  if (n_steps % 2 == 1) {
+    for (int mu = 0; mu < 4; ++mu)
+      if ((dirs >> mu) & 1u) {
+        lq_status st = cuda_check(cudaMemcpyAsync((char*)links + mu * db, (const char*)work + mu * db, db,
+                                                  cudaMemcpyDeviceToDevice, s),
+                                  "stout result copy");
+        if (st != LQ_OK) return st;
+      }
+  }
+  return LQ_OK;
+}
+
+TuneChoice stout_default_choice(int prec) {
+  TuneChoice c;
+  c.block = 128;
+  c.nsite = 1;
+  c.variant = 1;
+  (void)prec;
+  return c;
+}
+
+// Times one step of every candidate on a scratch output (links untouched).
+static lq_status stout_autotune(const lq_field* f, double rho, unsigned dirs, int reproject, cudaStream_t s,
+                                TuneChoice* best) {
+  void* tmp = nullptr;
+  lq_status st = scratch_alloc(&tmp, f->bytes, s, "stout autotune");
+  if (st != LQ_OK) return st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  *best = stout_default_choice(f->prec);
+  const int blocks[] = {64, 128, 256};
+  const int nsites[] = {1, 2, 4};
+  for (int b : blocks)
+    for (int ns : nsites) {
+      TuneChoice c;
+      c.block = b;
+      c.nsite = ns;
+      c.variant = 1;
+      st = launch_step(f->ptr, tmp, f->geom, f->prec, rho, dirs, reproject, c, s);  // warm-up
+      if (st != LQ_OK) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 2; ++r) launch_step(f->ptr, tmp, f->geom, f->prec, rho, dirs, reproject, c, s);
+      cudaEventRecord(e1, s);
+      st = cuda_check(cudaEventSynchronize(e1), "stout autotune timing");
+      if (st != LQ_OK) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        *best = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  scratch_free(tmp, s);
+  return st;
+}
+
+lq_status stout_choose(const lq_field* f, double rho, unsigned dirs, int reproject, const lq_stout_opts* o,
+                       cudaStream_t s, TuneChoice* out) {
+  if (o && o->block > 0) {
+    out->block = o->block;
+    out->nsite = o->sites_per_thread > 0 ? o->sites_per_thread : 1;
+    out->variant = o->variant > 0 ? o->variant : 1;
+    return LQ_OK;
+  }
+  *out = stout_default_choice(f->prec);
+  if (!tune_enabled()) return LQ_OK;
+  if (tune_get("stout", f->prec, f->geom.dims, dirs, out)) return LQ_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs != cudaStreamCaptureStatusNone) return LQ_OK;  // never tune inside a capture
+  lq_status st = stout_autotune(f, rho, dirs, reproject, s, out);
+  if (st != LQ_OK) return st;
+  tune_put("stout", f->prec, f->geom.dims, dirs, *out);
+  return LQ_OK;
+}
+
+// ---- CUDA-graph cache for the n-step sequence ------------------------------
+struct GraphKey {
+  void* links;
+  int dims[4];
+  int prec, n, reproject, block, nsite, variant, device;
+  unsigned dirs;
+  double rho;
+  bool operator<(const GraphKey& o) const { return std::memcmp(this, &o, sizeof(GraphKey)) < 0; }
+};
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  void* work = nullptr;
+};
+static std::mutex g_graph_mu;
+static std::map<GraphKey, GraphEntry>& graph_cache() {
+  static std::map<GraphKey, GraphEntry> m;
+  return m;
+}
+static void release_graphs() {
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  for (auto& kv : graph_cache()) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.work) cudaFree(kv.second.work);
+  }
+  graph_cache().clear();
+}
+
+static lq_status run_graph(lq_field* f, double rho, int n, unsigned dirs, int reproject, const TuneChoice& tc,
+                           cudaStream_t s) {
+  register_cache_release(release_graphs);
+  GraphKey k;
+  std::memset(&k, 0, sizeof(k));
+  k.links = f->ptr;
+  for (int i = 0; i < 4; ++i) k.dims[i] = f->geom.dims[i];
+  k.prec = f->prec;
+  k.n = n;
+  k.reproject = reproject;
+  k.block = tc.block;
+  k.nsite = tc.nsite;
+  k.variant = tc.variant;
+  k.device = current_device();
+  k.dirs = dirs;
+  k.rho = rho;
+  std::lock_guard<std::mutex> lk(g_graph_mu);
+  auto it = graph_cache().find(k);
+  if (it == graph_cache().end()) {
+    GraphEntry e;
+    lq_status st = cuda_check(cudaMalloc(&e.work, f->bytes), "stout graph workspace");
+    if (st != LQ_OK) return st;
+    cudaStream_t cap;
+    st = cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stout graph stream");
+    if (st != LQ_OK) {
+      cudaFree(e.work);
+      return st;
+    }
+    cudaGraph_t graph = nullptr;
+    st = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "stout graph capture");
+    if (st == LQ_OK) {
+      lq_status st_run = stout_run_steps(f->ptr, e.work, f->geom, f->prec, rho, n, dirs, reproject, tc, cap);
+      lq_status st_end = cuda_check(cudaStreamEndCapture(cap, &graph), "stout graph end capture");
+      st = st_run != LQ_OK ? st_run : st_end;
+    }
+    if (st == LQ_OK) st = cuda_check(cudaGraphInstantiate(&e.exec, graph, 0), "stout graph instantiate");
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    if (st != LQ_OK) {
+      cudaFree(e.work);
+      return st;
+    }
+    it = graph_cache().emplace(k, e).first;
+  }
+  return cuda_check(cudaGraphLaunch(it->second.exec, s), "stout graph launch");
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+extern "C" lq_status lq_stout_smear(lq_field* links, double rho, int n_steps, unsigned dirs_mask,
+                                    const lq_stout_opts* opts, void* stream) {
+  clear_error();
+  lq_status st = check_links(links, "lq_stout_smear");
+  if (st != LQ_OK) return st;
+  if ((st = check_dirs(dirs_mask, "lq_stout_smear")) != LQ_OK) return st;
+  if (!(rho >= 0.0) || rho > 1e6) {
+    set_error("lq_stout_smear: rho must be finite and >= 0");
+    return LQ_ERR_ARG;
+  }
+  if (n_steps < 0) {
+    set_error("lq_stout_smear: n_steps must be >= 0");
+    return LQ_ERR_ARG;
+  }
+  const lq_stout_opts* o = (opts && opts->struct_size >= (int)sizeof(lq_stout_opts)) ? opts : nullptr;
+  if (opts && !o && opts->struct_size != 0) {
+    set_error("lq_stout_smear: opts->struct_size %d < sizeof(lq_stout_opts)", opts->struct_size);
+    return LQ_ERR_ARG;
+  }
+  if (o && o->variant > 1) {
+    set_error("lq_stout_smear: variant %d is not available", o->variant);
+    return LQ_ERR_UNSUPPORTED;
+  }
+  if (o && o->block > 0 && (o->block % 32 != 0 || o->block > 256)) {
+    set_error("lq_stout_smear: block %d must be a multiple of 32 in [32, 256]", o->block);
+    return LQ_ERR_ARG;
+  }
+  if (n_steps == 0) return LQ_OK;
+  cudaStream_t s = as_stream(stream);
+  const int reproject = (o && o->reproject >= 0) ? o->reproject : (links->prec == LQ_F32 ? 1 : 0);
+  TuneChoice tc;
+  if ((st = stout_choose(links, rho, dirs_mask, reproject, o, s, &tc)) != LQ_OK) return st;
+  if (o && o->use_graph) return run_graph(links, rho, n_steps, dirs_mask, reproject, tc, s);
+  void* work = nullptr;
+  bool own = false;
+  if (o && o->work) {
+    if (o->work_bytes < links->bytes || (((uintptr_t)o->work) & 15u)) {
+      set_error("lq_stout_smear: opts->work must be 16-byte aligned and hold %zu bytes", links->bytes);
+      return LQ_ERR_ARG;
+    }
+    work = o->work;
+  } else {
+    if ((st = scratch_alloc(&work, links->bytes, s, "lq_stout_smear workspace")) != LQ_OK) return st;
+    own = true;
+  }
+  st = stout_run_steps(links->ptr, work, links->geom, links->prec, rho, n_steps, dirs_mask, reproject, tc, s);
+  if (own) scratch_free(work, s);
+  return st;
+}

@@ -1,0 +1,247 @@
+// Per-link stout smearing arithmetic (Morningstar & Peardon 2004, Secs. II-III):
+// staple sum, Omega = C U^dag, Q, Cayley-Hamilton coefficients f0,f1,f2 (always
+// FP64), exp(iQ) = f0 + f1 Q + f2 Q^2, U' = exp(iQ) U, optional FP64 SU(3)
+// re-projection.  Shared by the single-lattice, batched and backward kernels.
+#pragma once
+
+#include "lq_internal.h"
+#include "su3.cuh"
+
+namespace lq {
+
+// ---- periodic neighbours by index arithmetic (no site table) -------------
+__device__ __forceinline__ void site_coords(const GeomArgs& g, int s, int c[4]) {
+  int r = s;
+  c[0] = r % g.L[0];
+  r /= g.L[0];
+  c[1] = r % g.L[1];
+  r /= g.L[1];
+  c[2] = r % g.L[2];
+  c[3] = r / g.L[2];
+}
+// site of x + nu, where x has coordinate c_nu along nu
+__device__ __forceinline__ int nb_fwd(const GeomArgs& g, int s, int c_nu, int nu) {
+  return (c_nu + 1 < g.L[nu]) ? s + g.stride[nu] : s - (g.L[nu] - 1) * g.stride[nu];
+}
+__device__ __forceinline__ int nb_bwd(const GeomArgs& g, int s, int c_nu, int nu) {
+  return (c_nu > 0) ? s - g.stride[nu] : s + (g.L[nu] - 1) * g.stride[nu];
+}
+
+template <typename R>
+__device__ __forceinline__ M3<R> ld_link(const typename vec2<R>::type* __restrict__ U, long long V,
+                                         int dir, int s) {
+  return ld_m3<R>(U + (long long)dir * 9 * V + s, V);
+}
+
+// sum over nu in dirs, nu != mu, of
+//   U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+template <typename R>
+__device__ __forceinline__ M3<R> staple_sum(const typename vec2<R>::type* __restrict__ U,
+                                            const GeomArgs& g, int s, const int c[4], int mu,
+                                            unsigned dirs) {
+  const long long V = g.V;
+  M3<R> C;
+  m_zero(C);
+  const int s_pmu = nb_fwd(g, s, c[mu], mu);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu || !((dirs >> nu) & 1u)) continue;
+    const int s_pnu = nb_fwd(g, s, c[nu], nu);
+    const int s_mnu = nb_bwd(g, s, c[nu], nu);
+    const int s_pmu_mnu = nb_bwd(g, s_pmu, c[nu], nu);
+    {
+      M3<R> t = mul_nd(ld_link<R>(U, V, mu, s_pnu), ld_link<R>(U, V, nu, s_pmu));
+      mac_nn(C, ld_link<R>(U, V, nu, s), t);
+    }
+    {
+      M3<R> t = mul_nn(ld_link<R>(U, V, mu, s_mnu), ld_link<R>(U, V, nu, s_pmu_mnu));
+      mac_dn(C, ld_link<R>(U, V, nu, s_mnu), t);
+    }
+  }
+  return C;
+}
+
+// Hermitian traceless Q in compact form: real diagonal d0,d1,d2 and the upper
+// off-diagonals o01, o02, o12 (Q_kj = conj(Q_jk)).
+template <typename R> struct QH {
+  R d0, d1, d2;
+  cx<R> o01, o02, o12;
+};
+
+// Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega)
+template <typename R> __device__ __forceinline__ QH<R> q_from_omega(const M3<R>& om) {
+  QH<R> q;
+  R t = (om.e[0].im + om.e[4].im + om.e[8].im) * R(1.0 / 3.0);
+  q.d0 = om.e[0].im - t;
+  q.d1 = om.e[4].im - t;
+  q.d2 = om.e[8].im - t;
+  // Q_jk = (i/2)(conj(Om_kj) - Om_jk) = ((Om_kj.im + Om_jk.im)/2, (Om_kj.re - Om_jk.re)/2)
+  q.o01 = mkc<R>(R(0.5) * (om.e[3].im + om.e[1].im), R(0.5) * (om.e[3].re - om.e[1].re));
+  q.o02 = mkc<R>(R(0.5) * (om.e[6].im + om.e[2].im), R(0.5) * (om.e[6].re - om.e[2].re));
+  q.o12 = mkc<R>(R(0.5) * (om.e[7].im + om.e[5].im), R(0.5) * (om.e[7].re - om.e[5].re));
+  return q;
+}
+
+template <typename R> __device__ __forceinline__ R cnorm2(cx<R> a) { return fmaR(a.re, a.re, a.im * a.im); }
+
+// Q^2 of a compact Hermitian Q, again Hermitian (compact).
+template <typename R> __device__ __forceinline__ QH<R> q_square(const QH<R>& q) {
+  QH<R> r;
+  const R n01 = cnorm2(q.o01), n02 = cnorm2(q.o02), n12 = cnorm2(q.o12);
+  r.d0 = fmaR(q.d0, q.d0, n01 + n02);
+  r.d1 = fmaR(q.d1, q.d1, n01 + n12);
+  r.d2 = fmaR(q.d2, q.d2, n02 + n12);
+  // (Q^2)_01 = Q01 (d0 + d1) + Q02 conj(Q12)
+  r.o01 = cfma_nc(q.o02, q.o12, cscale(q.o01, q.d0 + q.d1));
+  // (Q^2)_02 = Q02 (d0 + d2) + Q01 Q12
+  r.o02 = cfma(q.o01, q.o12, cscale(q.o02, q.d0 + q.d2));
+  // (Q^2)_12 = conj(Q01) Q02 + Q12 (d1 + d2)
+  r.o12 = cfma_cn(q.o01, q.o02, cscale(q.o12, q.d1 + q.d2));
+  return r;
+}
+
+// Threshold on c1 below which the Q -> 0 limit f = (1, i, -1/2) is used, and
+// |w| at or below which xi0(w) = sin(w)/w uses its Taylor series.
+#define LQ_C1_SERIES 1e-28
+#define LQ_XI0_SERIES 0.05
+
+struct CHCoef {
+  cx<double> f0, f1, f2;
+};
+
+// Cayley-Hamilton coefficients of exp(iQ) = f0 + f1 Q + f2 Q^2, in FP64
+// (Morningstar & Peardon 2004, Sec. III).  The input Q is re-made exactly
+// traceless in FP64 first.
+__device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d2, cx<double> o01,
+                                                  cx<double> o02, cx<double> o12) {
+  CHCoef f;
+  const double tq = (d0 + d1 + d2) * (1.0 / 3.0);
+  d0 -= tq;
+  d1 -= tq;
+  d2 -= tq;
+  const double n01 = cnorm2(o01), n02 = cnorm2(o02), n12 = cnorm2(o12);
+  const double c1 = 0.5 * (d0 * d0 + d1 * d1 + d2 * d2) + n01 + n02 + n12;
+  // det Q = d0 d1 d2 - d0|o12|^2 - d1|o02|^2 - d2|o01|^2 + 2 Re(o01 o12 conj(o02))
+  const cx<double> p = cmul(o01, o12);
+  const double re3 = p.re * o02.re + p.im * o02.im;
+  const double c0 = d0 * d1 * d2 - d0 * n12 - d1 * n02 - d2 * n01 + 2.0 * re3;
+  if (!(c1 >= LQ_C1_SERIES)) {  // also catches NaN
+    f.f0 = mkc(1.0, 0.0);
+    f.f1 = mkc(0.0, 1.0);
+    f.f2 = mkc(-0.5, 0.0);
+    return f;
+  }
+  const bool neg = c0 < 0.0;
+  const double s3 = sqrt(c1 * (1.0 / 3.0));
+  const double c0max = 2.0 * s3 * s3 * s3;
+  const double x = fmin(fabs(c0) / c0max, 1.0);
+  const double theta = acos(x);
+  double st, ct;
+  sincos(theta * (1.0 / 3.0), &st, &ct);
+  const double u = s3 * ct;
+  const double w = sqrt(c1) * st;
+  const double u2 = u * u, w2 = w * w;
+  double sw, cw;
+  sincos(w, &sw, &cw);
+  const double xi0 = (fabs(w) <= LQ_XI0_SERIES)
+                         ? 1.0 - w2 * (1.0 / 6.0) * (1.0 - w2 * (1.0 / 20.0) * (1.0 - w2 * (1.0 / 42.0)))
+                         : sw / w;
+  double su, cu;
+  sincos(u, &su, &cu);
+  const cx<double> emiu = mkc(cu, -su);
+  const cx<double> e2iu = mkc(cu * cu - su * su, 2.0 * su * cu);
+  // h0 = (u^2 - w^2) e^{2iu} + e^{-iu} [8u^2 cos w + 2iu(3u^2 + w^2) xi0]
+  const cx<double> h0 = cadd(cscale(e2iu, u2 - w2),
+                             cmul(emiu, mkc(8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0)));
+  // h1 = 2u e^{2iu} - e^{-iu} [2u cos w - i(3u^2 - w^2) xi0]
+  const cx<double> h1 = csub(cscale(e2iu, 2.0 * u), cmul(emiu, mkc(2.0 * u * cw, -(3.0 * u2 - w2) * xi0)));
+  // h2 = e^{2iu} - e^{-iu} [cos w + 3iu xi0]
+  const cx<double> h2 = csub(e2iu, cmul(emiu, mkc(cw, 3.0 * u * xi0)));
+  const double inv = 1.0 / (9.0 * u2 - w2);
+  f.f0 = cscale(h0, inv);
+  f.f1 = cscale(h1, inv);
+  f.f2 = cscale(h2, inv);
+  if (neg) {  // f_j(-c0) = (-1)^j conj(f_j(c0))
+    f.f0 = cconj(f.f0);
+    f.f1 = mkc(-f.f1.re, f.f1.im);
+    f.f2 = cconj(f.f2);
+  }
+  return f;
+}
+
+// exp(iQ) = f0 + f1 Q + f2 Q^2 as a full matrix.
+template <typename R>
+__device__ __forceinline__ M3<R> expiq_assemble(const QH<R>& q, const QH<R>& q2, cx<R> f0, cx<R> f1,
+                                                cx<R> f2) {
+  M3<R> e;
+  e.e[0] = cadd(f0, mkc(f1.re * q.d0 + f2.re * q2.d0, f1.im * q.d0 + f2.im * q2.d0));
+  e.e[4] = cadd(f0, mkc(f1.re * q.d1 + f2.re * q2.d1, f1.im * q.d1 + f2.im * q2.d1));
+  e.e[8] = cadd(f0, mkc(f1.re * q.d2 + f2.re * q2.d2, f1.im * q.d2 + f2.im * q2.d2));
+  e.e[1] = cfma(f2, q2.o01, cmul(f1, q.o01));
+  e.e[2] = cfma(f2, q2.o02, cmul(f1, q.o02));
+  e.e[5] = cfma(f2, q2.o12, cmul(f1, q.o12));
+  e.e[3] = cfma(f2, cconj(q2.o01), cmul(f1, cconj(q.o01)));
+  e.e[6] = cfma(f2, cconj(q2.o02), cmul(f1, cconj(q.o02)));
+  e.e[7] = cfma(f2, cconj(q2.o12), cmul(f1, cconj(q.o12)));
+  return e;
+}
+
+// SU(3) re-projection in FP64: Gram-Schmidt of rows 0 and 1, row 2 = conj(row0 x row1).
+__device__ __forceinline__ void reproject_f64(M3<double>& m) {
+  double n0 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) n0 += cnorm2(m.e[k]);
+  const double r0 = rsqrt(n0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) m.e[k] = cscale(m.e[k], r0);
+  cx<double> p = mkc(0.0, 0.0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) p = cfma_cn(m.e[k], m.e[3 + k], p);  // sum conj(r0_k) row1_k
+  double n1 = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    m.e[3 + k] = csub(m.e[3 + k], cmul(p, m.e[k]));
+    n1 += cnorm2(m.e[3 + k]);
+  }
+  const double r1 = rsqrt(n1);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) m.e[3 + k] = cscale(m.e[3 + k], r1);
+  // row2 = conj(row0 x row1)
+  m.e[6] = cconj(csub(cmul(m.e[1], m.e[5]), cmul(m.e[2], m.e[4])));
+  m.e[7] = cconj(csub(cmul(m.e[2], m.e[3]), cmul(m.e[0], m.e[5])));
+  m.e[8] = cconj(csub(cmul(m.e[0], m.e[4]), cmul(m.e[1], m.e[3])));
+}
+
+template <typename A, typename B> __device__ __forceinline__ M3<A> m_convert(const M3<B>& m) {
+  M3<A> r;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) r.e[i] = mkc<A>((A)m.e[i].re, (A)m.e[i].im);
+  return r;
+}
+
+// New link U'_mu(x) for one (site, mu): FP64 coefficients always; matrix
+// algebra in R; optional FP64 re-projection.
+template <typename R>
+__device__ __forceinline__ M3<R> stout_link(const typename vec2<R>::type* __restrict__ U,
+                                            const GeomArgs& g, int s, const int c[4], int mu,
+                                            unsigned dirs, R rho, bool reproject) {
+  const M3<R> C = m_rscale(staple_sum<R>(U, g, s, c, mu, dirs), rho);
+  const M3<R> Umu = ld_link<R>(U, g.V, mu, s);
+  const M3<R> Om = mul_nd(C, Umu);
+  const QH<R> q = q_from_omega(Om);
+  const CHCoef f = ch_coefficients((double)q.d0, (double)q.d1, (double)q.d2,
+                                   mkc<double>(q.o01.re, q.o01.im), mkc<double>(q.o02.re, q.o02.im),
+                                   mkc<double>(q.o12.re, q.o12.im));
+  const QH<R> q2 = q_square(q);
+  const M3<R> E = expiq_assemble(q, q2, mkc<R>((R)f.f0.re, (R)f.f0.im), mkc<R>((R)f.f1.re, (R)f.f1.im),
+                                 mkc<R>((R)f.f2.re, (R)f.f2.im));
+  M3<R> Up = mul_nn(E, Umu);
+  if (reproject) {
+    M3<double> d = m_convert<double, R>(Up);
+    reproject_f64(d);
+    Up = m_convert<R, double>(d);
+  }
+  return Up;
+}
+
+}  // namespace lq

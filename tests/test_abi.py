@@ -1,0 +1,102 @@
+"""The C-ABI library loads, exports every entry point include/lqcd.h declares,
+and validates arguments on the host (no device work is launched here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "lqcd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lq_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lqlib):
+    lib = lqlib.capi()
+    names = header_functions()
+    assert len(names) >= 24
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_declares_every_symbol(lqlib):
+    from paper_1105_2279_gb300 import _lib
+    assert set(header_functions()) == set(_lib.SIGNATURES)
+
+
+def test_abi_version_and_geometry(lqlib):
+    lib = lqlib.capi()
+    assert lib.lq_abi_version() == 1
+    g = lqlib.Geometry((3, 4, 5, 6))
+    dims, vol = lqlib.geom_info(g)
+    assert dims == (3, 4, 5, 6) and vol == 360
+    assert lqlib.field_bytes(g, lqlib.LQ_LINKS, lqlib.LQ_F64) == 360 * 36 * 16
+    assert lqlib.field_bytes(g, lqlib.LQ_REAL, lqlib.LQ_F32) == 360 * 4
+    assert lqlib.field_bytes(g, lqlib.LQ_COLOR_VECTOR, lqlib.LQ_F32) == 360 * 3 * 8
+
+
+@pytest.mark.parametrize("dims", [(0, 4, 4, 4), (4, -1, 4, 4), (2048, 2048, 1024, 1)])
+def test_bad_geometry_rejected(lqlib, dims):
+    with pytest.raises(lqlib.LqError) as e:
+        lqlib.Geometry(dims)
+    assert e.value.status == -1
+    assert "lq_geom_create" in str(e.value)
+
+
+def test_wrap_validation(lqlib):
+    lib = lqlib.capi()
+    g = lqlib.Geometry((2, 2, 2, 2))
+    h = ctypes.c_void_p()
+    need = lqlib.field_bytes(g, lqlib.LQ_LINKS, lqlib.LQ_F64)
+    # misaligned pointer, too few bytes, bad kind
+    assert lib.lq_field_wrap(g.handle, 0, 1, ctypes.c_void_p(0x1008), need, ctypes.byref(h)) == -1
+    assert b"aligned" in lib.lq_last_error()
+    assert lib.lq_field_wrap(g.handle, 0, 1, ctypes.c_void_p(0x1000), need - 1, ctypes.byref(h)) == -1
+    assert lib.lq_field_wrap(g.handle, 9, 1, ctypes.c_void_p(0x1000), need, ctypes.byref(h)) == -1
+    assert lib.lq_field_wrap(g.handle, 0, 1, ctypes.c_void_p(0x1000), need, ctypes.byref(h)) == 0
+    f = h
+    # stout argument checks happen before any device work
+    assert lib.lq_stout_smear(f, 0.1, 1, 0, None, None) == -1
+    assert lib.lq_stout_smear(f, 0.1, 1, 16, None, None) == -1
+    assert lib.lq_stout_smear(f, -0.1, 1, 15, None, None) == -1
+    assert lib.lq_stout_smear(f, float("nan"), 1, 15, None, None) == -1
+    assert lib.lq_stout_smear(f, 0.1, -1, 15, None, None) == -1
+    assert lib.lq_stout_smear(f, 0.1, 0, 15, None, None) == 0      # zero steps: nothing to do
+    assert lib.lq_stout_smear(None, 0.1, 1, 15, None, None) == -1
+    # shift of a field onto itself, bad direction
+    assert lib.lq_shift(f, f, 0, 1, None) == -1
+    assert lib.lq_shift(f, f, 4, 1, None) == -1
+    assert lib.lq_plaquette(None, None, None) == -1
+    assert lib.lq_field_free(f) == 0
+
+
+def test_kind_mismatch_is_geom_error(lqlib):
+    lib = lqlib.capi()
+    g = lqlib.Geometry((2, 2, 2, 2))
+    h = ctypes.c_void_p()
+    assert lib.lq_field_wrap(g.handle, 1, 1, ctypes.c_void_p(0x1000), 1 << 20, ctypes.byref(h)) == 0
+    assert lib.lq_stout_smear(h, 0.1, 1, 15, None, None) == -2
+    out = (ctypes.c_double * 3)()
+    assert lib.lq_plaquette(h, out, None) == -2
+    lib.lq_field_free(h)
+
+
+def test_expr_program_validation(lqlib):
+    lib = lqlib.capi()
+    g = lqlib.Geometry((2, 2, 2, 2))
+    h = ctypes.c_void_p()
+    assert lib.lq_field_wrap(g.handle, 0, 1, ctypes.c_void_p(0x1000), 1 << 20, ctypes.byref(h)) == 0
+    red = (ctypes.c_double * 2)()
+    ops = (ctypes.c_void_p * 1)(h)
+    # program without a final STORE, register out of range, operand out of range
+    for prog in ([("loadl", 0, 0, 0, 0, 0)],
+                 [("loadl", 9, 0, 0, 0, 0), ("store", 9)],
+                 [("loadl", 0, 3, 0, 0, 0), ("store", 0)],
+                 [("loadl", 0, 0, 5, 0, 0), ("store", 0)]):
+        arr, n = lqlib.compile_program(prog)
+        assert lib.lq_expr_eval(None, arr, n, ops, 1, red, None) == -1
+    lib.lq_field_free(h)

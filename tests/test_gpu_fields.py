@@ -1,0 +1,156 @@
+"""GPU reductions, shift, expression programs and transfers through the C ABI
+vs the oracle.
+
+Reductions accumulate in FP64: FP64 fields agree with the oracle to 1e-13
+relative (different summation order); FP32 fields to 1e-6 relative.  Shift
+and upload/download are bit exact.  Reductions are bit-identical run to run.
+"""
+import numpy as np
+import pytest
+
+import fieldgen
+import paper_1105_2279_gb300 as lq
+from oracle import expr, gauge, lattice
+from tests.gpu_util import upload_links
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_upload_download_roundtrip(gpu, prec):
+    dims = (3, 5, 2, 7)
+    U = fieldgen.haar_su3(dims, 200)
+    f = upload_links(U, prec)
+    back = f.download()
+    want = U if prec == lq.LQ_F64 else U.astype(np.complex64)
+    assert np.array_equal(back, want)
+    # device layout is [dir][comp][site] (re, im)
+    t = f.tensor.cpu().numpy()
+    s = lattice.site_index(1, 3, 1, 4, dims)
+    assert t[2, 5, s, 0] == want[4, 1, 3, 1, 2, 1, 2].real
+    assert t[2, 5, s, 1] == want[4, 1, 3, 1, 2, 1, 2].imag
+
+
+@pytest.mark.parametrize("dims,gen", [((4, 4, 4, 4), "haar"), ((2, 2, 2, 2), "near"),
+                                      ((3, 4, 5, 6), "near"), ((8, 8, 8, 16), "near")])
+def test_plaquette(gpu, dims, gen):
+    U = fieldgen.haar_su3(dims, 201) if gen == "haar" else fieldgen.near_identity_su3(dims, 201)
+    ref = gauge.plaquette(U)
+    f64 = upload_links(U, lq.LQ_F64)
+    got = lq.plaquette(f64)
+    assert np.allclose(got, ref, rtol=0, atol=1e-14)
+    assert lq.plaquette(f64) == got          # deterministic
+    f32 = upload_links(U, lq.LQ_F32)
+    assert np.allclose(lq.plaquette(f32), ref, rtol=0, atol=2e-6)
+    S = lq.wilson_action(f64, 6.0)
+    assert abs(S - gauge.wilson_action(U, 6.0)) < 1e-12 * max(1.0, abs(S))
+
+
+def test_unit_plaquette_exact(gpu):
+    f = upload_links(fieldgen.unit_links((3, 4, 5, 2)), lq.LQ_F64)
+    assert lq.plaquette(f) == (1.0, 1.0, 1.0)
+    assert lq.wilson_action(f, 6.0) == 0.0
+
+
+@pytest.mark.parametrize("kind", [lq.LQ_LINKS, lq.LQ_COLOR_MATRIX, lq.LQ_COLOR_VECTOR, lq.LQ_COMPLEX, lq.LQ_REAL])
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_shift_all_kinds(gpu, kind, prec):
+    dims = (3, 4, 5, 2)
+    g = lq.Geometry(dims)
+    rng = np.random.default_rng(202)
+    shape = lattice.field_shape(dims) + lq.SITE_SHAPE[kind]
+    a = rng.standard_normal(shape) + (0 if kind == lq.LQ_REAL else 1j * rng.standard_normal(shape))
+    fin = lq.Field.from_host(g, kind, prec, a)
+    fout = lq.Field(g, kind, prec)
+    host = a.astype(fin.host_dtype())
+    for mu in range(4):
+        for sign in (1, -1):
+            lq.shift(fout, fin, mu, sign)
+            assert np.array_equal(fout.download(), lattice.shift(host, mu, sign))
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_reduce_sum_and_trace(gpu, prec):
+    dims = (5, 3, 4, 3)
+    U = fieldgen.haar_su3(dims, 203)
+    f = upload_links(U, prec)
+    tol = 1e-12 if prec == lq.LQ_F64 else 1e-5
+    ref_sum = complex(np.sum(U.astype(f.host_dtype()).astype(np.complex128)))
+    assert abs(lq.reduce_sum(f) - ref_sum) < tol * max(1, abs(ref_sum))
+    ref_tr = complex(np.sum(np.trace(U.astype(f.host_dtype()).astype(np.complex128), axis1=-2, axis2=-1)))
+    assert abs(lq.reduce_trace(f) - ref_tr) < tol * max(1, abs(ref_tr))
+    g = lq.Geometry(dims)
+    r = np.random.default_rng(204).standard_normal(lattice.field_shape(dims))
+    fr = lq.Field.from_host(g, lq.LQ_REAL, prec, r)
+    assert abs(lq.reduce_sum(fr).real - r.astype(fr.host_dtype()).astype(np.float64).sum()) < tol * 100
+
+
+def micro_suite_programs():
+    """Programs of the micro-suite on a links operand (index 0)."""
+    # sum_mu tr(U_mu(x) U_mu(x+mu))
+    p_tr = []
+    for mu in range(4):
+        p_tr += [("loadl", 0, 0, mu, 0, 0), ("loadl", 1, 0, mu, mu, +1), ("mul", 2, 0, 1)]
+        p_tr += [("add", 3, 3, 2)] if mu else [("add", 3, 2, 2), ("sub", 3, 3, 2)]
+    p_tr += [("store", 3)]
+    # U_mu(x) U_nu(x+mu)^dag for (mu, nu) = (0, 1) and (2, 3)
+    p_adj = [[("loadl", 0, 0, mu, 0, 0), ("loadl", 1, 0, nu, mu, +1), ("adj", 2, 1), ("mul", 3, 0, 2), ("store", 3)]
+             for mu, nu in [(0, 1), (2, 3)]]
+    return p_tr, p_adj
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_micro_suite_expressions(gpu, prec):
+    dims = (6, 4, 5, 8)
+    U = fieldgen.near_identity_su3(dims, 205)
+    g = lq.Geometry(dims)
+    fU = upload_links(U, prec)
+    p_tr, p_adj = micro_suite_programs()
+    tol = 1e-12 if prec == lq.LQ_F64 else 2e-5
+    got = lq.expr_eval(p_tr, [fU], reduce=True)
+    ref = expr.trace_sum(expr.eval_program(p_tr, [U]))
+    assert abs(got - ref) < tol * max(1.0, abs(ref))
+    for p in p_adj:
+        out = lq.Field(g, lq.LQ_COLOR_MATRIX, prec)
+        red = lq.expr_eval(p, [fU], out=out, reduce=True)
+        ref_field = expr.eval_program(p, [U])
+        assert np.max(np.abs(out.download() - ref_field)) < (1e-14 if prec == lq.LQ_F64 else 1e-6)
+        assert abs(red - expr.trace_sum(ref_field)) < tol * max(1.0, abs(red))
+
+
+def test_plaquette_program_matches_plaquette(gpu):
+    dims = (4, 3, 4, 5)
+    U = fieldgen.near_identity_su3(dims, 206)
+    fU = upload_links(U, lq.LQ_F64)
+    tot = 0.0
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            prog = [("loadl", 0, 0, mu, 0, 0), ("loadl", 1, 0, nu, mu, +1), ("loadl", 2, 0, mu, nu, +1),
+                    ("loadl", 3, 0, nu, 0, 0), ("mul", 4, 0, 1), ("adj", 5, 2), ("mul", 4, 4, 5), ("adj", 6, 3),
+                    ("mul", 4, 4, 6), ("retr", 7, 4), ("store", 7)]
+            tot += lq.expr_eval(prog, [fU], reduce=True).real / 3.0
+    assert abs(tot / (18 * lattice.volume(dims)) - lq.plaquette(fU)[0]) < 1e-13
+
+
+def test_jacobi_hopping_term_program(gpu):
+    """One Jacobi iteration of Listing 1 built from C-ABI expression programs
+    (colour-vector operand, shifts pushed to the loads) vs the oracle."""
+    dims = (4, 3, 4, 6)
+    U = fieldgen.haar_su3(dims, 207)
+    chi = fieldgen.color_vector(dims, 208)
+    g = lq.Geometry(dims)
+    fU = upload_links(U, lq.LQ_F64)
+    fchi = lq.Field.from_host(g, lq.LQ_COLOR_VECTOR, lq.LQ_F64, chi)
+    kappa = 0.21
+    prog = []
+    for mu in range(4):
+        # U_mu(x) chi(x+mu) + U_mu(x-mu)^dag chi(x-mu)
+        prog += [("loadl", 0, 0, mu, 0, 0), ("load", 1, 1, mu, +1), ("mul", 2, 0, 1),
+                 ("loadl", 3, 0, mu, mu, -1), ("adj", 3, 3), ("load", 4, 1, mu, -1), ("mul", 5, 3, 4),
+                 ("add", 2, 2, 5)]
+        prog += [("add", 6, 6, 2)] if mu else [("add", 6, 2, 2), ("sub", 6, 6, 2)]
+    prog += [("scale", 6, 6, kappa, 0.0), ("load", 7, 1, 0, 0), ("add", 6, 6, 7), ("store", 6)]
+    out = lq.Field(g, lq.LQ_COLOR_VECTOR, lq.LQ_F64)
+    lq.expr_eval(prog, [fU, fchi], out=out)
+    ref = expr.jacobi_smear(U, chi, kappa, 1, 1.0)
+    assert np.max(np.abs(out.download() - ref)) < 1e-13

@@ -1,0 +1,163 @@
+"""GPU stout smearing through the C ABI vs the FP64 oracle.
+
+FP64 path: max |U_gpu - U_oracle| <= 1e-12 per link element (elements of SU(3)
+matrices are at most 1 in magnitude, so this is also the relative error with
+respect to the link).  FP32 path (FP32 matrix algebra, FP64 Cayley-Hamilton
+coefficients and re-projection): per-element error <= 2e-6 per step taken
+(FP32 rounding of ~3k operations per link, ~1e-7 each, accumulated over
+steps), unitarity <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import fieldgen
+import paper_1105_2279_gb300 as lq
+from oracle import gauge, lattice, stout
+from oracle.su3 import unitarity_violation
+from tests.gpu_util import links_err, upload_links
+
+pytestmark = pytest.mark.gpu
+ALL, SPATIAL = (0, 1, 2, 3), (0, 1, 2)
+F64_TOL = 1e-12
+F32_TOL_PER_STEP = 2e-6
+
+
+def _run(U, prec, rho, n, dirs, **opts):
+    f = upload_links(U, prec)
+    lq.stout_smear(f, rho, n, dirs, **opts)
+    return f.download()
+
+
+@pytest.mark.parametrize("dims,gen,rho,n,dirs", [
+    ((4, 4, 4, 4), "haar", 0.1, 1, ALL),          # the 4^4 plain-method workload
+    ((2, 2, 2, 2), "haar", 0.1, 2, ALL),          # x+mu == x-mu
+    ((3, 4, 5, 6), "near", 0.125, 3, ALL),        # odd extents, V not a multiple of any block
+    ((3, 4, 5, 6), "near", 0.1, 3, SPATIAL),
+    ((5, 3, 2, 7), "haar", 0.25, 2, (1, 3)),
+    ((6, 6, 6, 12), "near", 0.1, 4, ALL),
+    ((8, 8, 8, 16), "near", 0.1, 2, SPATIAL),
+])
+def test_f64_matches_oracle(gpu, dims, gen, rho, n, dirs):
+    U = fieldgen.haar_su3(dims, 100) if gen == "haar" else fieldgen.near_identity_su3(dims, 100)
+    ref = stout.stout_smear(U, rho, n, dirs)
+    got = _run(U, lq.LQ_F64, rho, n, dirs)
+    a, r = links_err(got, ref)
+    assert a <= F64_TOL and r <= F64_TOL, (a, r)
+    for mu in range(4):
+        if mu not in dirs:
+            assert np.array_equal(got[..., mu, :, :], U[..., mu, :, :])
+
+
+@pytest.mark.parametrize("dims,gen,rho,n,dirs", [
+    ((4, 4, 4, 4), "haar", 0.1, 1, ALL),
+    ((3, 4, 5, 6), "near", 0.125, 3, ALL),
+    ((6, 5, 4, 8), "near", 0.1, 6, SPATIAL),
+    ((2, 2, 2, 2), "haar", 0.1, 2, ALL),
+])
+def test_f32_mixed_matches_oracle(gpu, dims, gen, rho, n, dirs):
+    U = fieldgen.haar_su3(dims, 101) if gen == "haar" else fieldgen.near_identity_su3(dims, 101)
+    ref = stout.stout_smear(U, rho, n, dirs)
+    got = _run(U, lq.LQ_F32, rho, n, dirs)
+    a, _ = links_err(got, ref)
+    assert a <= F32_TOL_PER_STEP * n, a
+    du, dd = unitarity_violation(got.astype(np.complex128))
+    assert du < 1e-6 and dd < 1e-6, (du, dd)
+
+
+def test_unit_field_and_rho_zero(gpu):
+    dims = (4, 3, 2, 5)
+    U1 = fieldgen.unit_links(dims)
+    for prec in (lq.LQ_F64, lq.LQ_F32):
+        got = _run(U1, prec, 0.2, 3, ALL)
+        assert np.array_equal(got.astype(np.complex128), U1)
+    U = fieldgen.haar_su3(dims, 102)
+    got = _run(U, lq.LQ_F64, 0.0, 2, ALL)
+    assert np.array_equal(got, U)
+
+
+def test_unitarity_f64(gpu):
+    U = fieldgen.haar_su3((4, 4, 4, 4), 103)
+    got = _run(U, lq.LQ_F64, 0.125, 5, ALL)
+    du, dd = unitarity_violation(got)
+    assert du < 1e-13 and dd < 1e-13
+
+
+def test_gauge_covariance_gpu(gpu):
+    dims = (4, 3, 4, 3)
+    U = fieldgen.haar_su3(dims, 104)
+    g = fieldgen.gauge_field_g(dims, 105)
+    a = _run(gauge.gauge_transform(U, g), lq.LQ_F64, 0.1, 2, ALL)
+    b = gauge.gauge_transform(_run(U, lq.LQ_F64, 0.1, 2, ALL), g)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_launch_shapes_graph_and_workspace_agree_bitwise(gpu, prec):
+    import torch
+    dims = (5, 6, 3, 7)
+    U = fieldgen.near_identity_su3(dims, 106)
+    base = _run(U, prec, 0.1, 3, ALL)
+    for block, ns in [(32, 1), (64, 2), (256, 4), (128, 3)]:
+        got = _run(U, prec, 0.1, 3, ALL, block=block, sites_per_thread=ns)
+        assert np.array_equal(got, base), (block, ns)
+    for _ in range(2):   # graph recorded on the first call, replayed on the second
+        assert np.array_equal(_run(U, prec, 0.1, 3, ALL, use_graph=True), base)
+    f = upload_links(U, prec)
+    work = torch.empty_like(f.tensor)
+    lq.stout_smear(f, 0.1, 3, ALL, work=work)
+    assert np.array_equal(f.download(), base)
+
+
+def test_autotuner_keeps_results(gpu, tmp_path):
+    dims = (6, 4, 4, 8)
+    U = fieldgen.near_identity_su3(dims, 107)
+    base = _run(U, lq.LQ_F64, 0.1, 2, ALL, block=128, sites_per_thread=1)
+    path = str(tmp_path / "tune.txt")
+    lq.tune(path)
+    got = _run(U, lq.LQ_F64, 0.1, 2, ALL)
+    assert np.array_equal(got, base)
+    assert lq.tune_lookup(lq.LQ_F64, dims, ALL) is not None
+    assert "stout" in open(path).read()
+
+
+def test_16c32_ten_spatial_steps_f64(gpu):
+    """16^3 x 32, links exp(i 0.3 H), 10 steps rho = 0.1 over the spatial
+    directions, FP64: every link element against the oracle."""
+    dims = (16, 16, 16, 32)
+    U = fieldgen.near_identity_su3(dims, 1)
+    ref = stout.stout_smear(U, 0.1, 10, SPATIAL)
+    got = _run(U, lq.LQ_F64, 0.1, 10, SPATIAL)
+    a, r = links_err(got, ref)
+    assert a <= F64_TOL and r <= F64_TOL, (a, r)
+    p_ref = gauge.plaquette(ref)
+    f = upload_links(got, lq.LQ_F64)
+    assert np.allclose(lq.plaquette(f), p_ref, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_48c96_six_steps_sampled(gpu, prec):
+    """48^3 x 96, exp(i 0.3 H) links, 6 steps rho = 0.125 in 4 dims, in the launch
+    configuration the benchmark uses; sampled sites are checked against the
+    oracle run on periodic boxes of side 13 around them (6 steps reach at most
+    6 sites in every direction, so the box centre is exact)."""
+    import torch
+    dims = (48, 48, 48, 96)
+    n, rho = 6, 0.125
+    Ut = fieldgen.near_identity_su3_torch(dims, 2, device="cuda")
+    g = lq.Geometry(dims)
+    f = lq.Field(g, lq.LQ_LINKS, prec)
+    U = Ut.cpu().numpy()
+    del Ut
+    torch.cuda.empty_cache()
+    f.upload(U)
+    lq.stout_smear(f, rho, n, ALL)
+    got = f.download()
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for _ in range(6):
+        c = [int(rng.integers(L)) for L in dims]
+        box = lattice.sub_box(U, c, n)
+        ref = stout.stout_smear(box, rho, n, ALL)[n, n, n, n]
+        worst = max(worst, float(np.max(np.abs(got[c[3], c[2], c[1], c[0]].astype(np.complex128) - ref))))
+    tol = F64_TOL if prec == lq.LQ_F64 else F32_TOL_PER_STEP * n
+    assert worst <= tol, worst
