@@ -10,7 +10,9 @@ order and builds:
 * ``near_identity_su3`` U = exp(i*eps*H), H = (A + A^dag)/2 - tr(.)/3 with A
                         complex Gaussian (re, im ~ N(0,1)); the exponential of
                         the Hermitian matrix is taken through its
-                        eigendecomposition (numpy/torch ``eigh``).
+                        eigendecomposition (numpy ``eigh``); the large-lattice
+                        variant uses ``torch.linalg.matrix_exp`` on the device
+                        (same normals, same field up to rounding).
 * ``diagonal_phases``   abelian links diag(e^{ia}, e^{ib}, e^{-i(a+b)}).
 * ``gauge_field_g``     a Haar SU(3) matrix per site (gauge transformation).
 * ``su3_direction``     a random unit-norm traceless anti-Hermitian matrix.
@@ -66,9 +68,9 @@ def near_identity_su3(dims, seed, eps=0.3, ndir=4):
 
 
 def near_identity_su3_torch(dims, seed, eps=0.3, ndir=4, device="cuda", chunk=1 << 22):
-    """Same recipe for large lattices: normals from PCG64 on the host,
-    eigendecomposition by torch on `device`.  Returns a complex128 torch
-    tensor shaped (Lt, Lz, Ly, Lx, ndir, 3, 3) on `device`."""
+    """Same recipe for large lattices: normals from PCG64 on the host, the
+    exponential by torch.linalg.matrix_exp on `device`.  Returns a complex128
+    torch tensor shaped (Lt, Lz, Ly, Lx, ndir, 3, 3) on `device`."""
     import torch
     rng = np.random.default_rng(seed)
     shape = _shape(dims) + (ndir,)
@@ -79,9 +81,7 @@ def near_identity_su3_torch(dims, seed, eps=0.3, ndir=4, device="cuda", chunk=1 
         m = min(chunk, n - done)
         h = _traceless_hermitian(_complex_gauss(rng, (m, 3, 3)))
         ht = torch.from_numpy(h).to(device)
-        lam, v = torch.linalg.eigh(ht)
-        ph = torch.exp(1j * eps * lam)
-        out[done:done + m] = (v * ph[:, None, :]) @ v.conj().transpose(-1, -2)
+        out[done:done + m] = torch.linalg.matrix_exp((1j * eps) * ht)
         done += m
     return out.reshape(shape + (3, 3))
 

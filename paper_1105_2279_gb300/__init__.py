@@ -267,3 +267,78 @@ def geom_info(geom):
     v = c_longlong()
     _check(L.load().lq_geom_info(geom.handle, d, byref(v)), "lq_geom_info")
     return tuple(d), v.value
+
+
+def _prec_of(t):
+    import torch
+    if t.dtype == torch.float64:
+        return LQ_F64
+    if t.dtype == torch.float32:
+        return LQ_F32
+    raise TypeError("links tensors are float32 or float64, shaped [4, 9, V, 2]")
+
+
+def _autograd():
+    import torch
+
+    class StoutSmear(torch.autograd.Function):
+        """U -> stout^n(U) on a links tensor [4, 9, V, 2] (structure of arrays).
+
+        The gradient w.r.t. the tensor's real components is the field
+        G = dL/dRe U + i dL/dIm U in the same layout, which is exactly the seed
+        lq_stout_backward expects; its result is returned in the same form."""
+
+        @staticmethod
+        def forward(ctx, links, dims, rho, n_steps, dirs):
+            geom = Geometry(dims)
+            prec = _prec_of(links)
+            out = torch.empty_like(links)
+            out.copy_(links)
+            stout_smear(Field(geom, LQ_LINKS, prec, tensor=out), rho, n_steps, dirs)
+            ctx.save_for_backward(links)
+            ctx.args = (dims, rho, n_steps, dirs, prec)
+            return out
+
+        @staticmethod
+        def backward(ctx, grad):
+            (links,) = ctx.saved_tensors
+            dims, rho, n_steps, dirs, prec = ctx.args
+            geom = Geometry(dims)
+            thin = Field(geom, LQ_LINKS, prec, tensor=links.contiguous())
+            seed = Field(geom, LQ_LINKS, prec, tensor=grad.contiguous())
+            gout = Field(geom, LQ_LINKS, prec)
+            stout_backward(thin, rho, n_steps, dirs, None, grad_seed=seed, grad_out=gout)
+            return gout.tensor, None, None, None, None
+
+    class WilsonAction(torch.autograd.Function):
+        """S = beta sum_x sum_{mu<nu} (1 - Re tr P_{mu nu}(x)/3) of a links tensor (FP64 scalar)."""
+
+        @staticmethod
+        def forward(ctx, links, dims, beta):
+            geom = Geometry(dims)
+            prec = _prec_of(links)
+            s = wilson_action(Field(geom, LQ_LINKS, prec, tensor=links.contiguous()), beta)
+            ctx.save_for_backward(links)
+            ctx.args = (dims, beta, prec)
+            return torch.tensor(s, dtype=torch.float64, device=links.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            (links,) = ctx.saved_tensors
+            dims, beta, prec = ctx.args
+            geom = Geometry(dims)
+            thin = Field(geom, LQ_LINKS, prec, tensor=links.contiguous())
+            gout = Field(geom, LQ_LINKS, prec)
+            # the Wilson gradient is linear in beta: scale the upstream factor into it
+            stout_backward(thin, 0.0, 0, 15, None, beta=beta * float(grad), grad_out=gout)
+            return gout.tensor, None, None
+
+    return StoutSmear, WilsonAction
+
+
+def stout_smear_autograd(links, dims, rho, n_steps, dirs=(0, 1, 2, 3)):
+    return _autograd()[0].apply(links, tuple(dims), float(rho), int(n_steps), dirs_mask(dirs))
+
+
+def wilson_action_autograd(links, dims, beta):
+    return _autograd()[1].apply(links, tuple(dims), float(beta))

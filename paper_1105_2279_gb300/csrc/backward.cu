@@ -1,0 +1,305 @@
+// Stout force: gradient of a scalar through n stout steps (Morningstar &
+// Peardon 2004, Sec. IV), seeded by the Wilson-action gradient or by a given
+// gradient field, with per-step checkpoints and forward recomputation.
+//
+// Convention: G_U = dS/dRe U + i dS/dIm U, so dS = Re tr(G^dag dU).  One step
+// U -> U' (per smeared link: C = rho S, Omega = C U^dag, Q, E = exp(iQ),
+// U' = E U) maps G' = G_{U'} to G_U in two kernels:
+//   k_bwd_link:   per smeared link, G_E = G' U^dag,
+//                 M = tr(G_E^dag B1) Q + tr(G_E^dag B2) Q^2 + f1 G_E^dag + f2 (Q G_E^dag + G_E^dag Q)
+//                 with B_i = sum_j b_ij Q^j, G_Omega = TA(i M^dag);
+//                 writes G_U(local) = E^dag G' + G_Omega^dag C and K = rho G_Omega U
+//                 (the gradient w.r.t. the bare staple sum S).
+//   k_bwd_staple: per link, adds the six staple-insertion terms of K of the
+//                 neighbouring links (the six-term sum of the stout force).
+#include <algorithm>
+#include <vector>
+
+#include "lq_internal.h"
+#include "stout_core.cuh"
+
+namespace lq {
+
+template <typename R> using V2 = typename vec2<R>::type;
+
+template <typename R>
+__device__ __forceinline__ M3<R> qh_full(const QH<R>& q) {
+  M3<R> m;
+  m.e[0] = mkc<R>(q.d0, 0);
+  m.e[4] = mkc<R>(q.d1, 0);
+  m.e[8] = mkc<R>(q.d2, 0);
+  m.e[1] = q.o01;
+  m.e[2] = q.o02;
+  m.e[5] = q.o12;
+  m.e[3] = cconj(q.o01);
+  m.e[6] = cconj(q.o02);
+  m.e[7] = cconj(q.o12);
+  return m;
+}
+
+// sum_ij conj(A_ij) B_ij = tr(A^dag B)
+template <typename R> __device__ __forceinline__ cx<R> tr_dn(const M3<R>& a, const M3<R>& b) {
+  cx<R> t = mkc<R>(0, 0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) t = cfma_cn(a.e[i], b.e[i], t);
+  return t;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_bwd_link(const V2<R>* __restrict__ U, const V2<R>* __restrict__ Gp,
+                                                  V2<R>* __restrict__ Gout, V2<R>* __restrict__ K, GeomArgs g, R rho,
+                                                  unsigned dirs) {
+  const long long V = g.V;
+  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const int s = (int)sl;
+  const int mu = blockIdx.y;
+  const long long off = (long long)mu * 9 * V + s;
+  if (!((dirs >> mu) & 1u)) {  // not smeared: the gradient passes through
+    st_m3<R>(Gout + off, V, ld_m3<R>(Gp + off, V));
+    return;
+  }
+  int c[4];
+  site_coords(g, s, c);
+  const M3<R> C = m_rscale(staple_sum<R>(U, g, s, c, mu, dirs), rho);
+  const M3<R> Umu = ld_m3<R>(U + off, V);
+  const QH<R> q = q_from_omega(mul_nd(C, Umu));
+  const CHDeriv d = ch_coefficients_deriv((double)q.d0, (double)q.d1, (double)q.d2, mkc<double>(q.o01.re, q.o01.im),
+                                          mkc<double>(q.o02.re, q.o02.im), mkc<double>(q.o12.re, q.o12.im));
+  const QH<R> q2 = q_square(q);
+  const M3<R> Qf = qh_full(q), Q2f = qh_full(q2);
+  const M3<R> Gpm = ld_m3<R>(Gp + off, V);
+  const M3<R> GE = mul_nd(Gpm, Umu);  // G_E = G' U^dag
+  // tr(G_E^dag Q^j), j = 0, 1, 2
+  const cx<R> t0 = cconj(m_trace(GE));
+  const cx<R> t1 = tr_dn(GE, Qf);
+  const cx<R> t2 = tr_dn(GE, Q2f);
+  cx<double> a1 = mkc(0.0, 0.0), a2 = mkc(0.0, 0.0);
+  const cx<double> td[3] = {mkc<double>(t0.re, t0.im), mkc<double>(t1.re, t1.im), mkc<double>(t2.re, t2.im)};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    a1 = cfma(d.b1[j], td[j], a1);
+    a2 = cfma(d.b2[j], td[j], a2);
+  }
+  const cx<R> f1 = mkc<R>((R)d.f[1].re, (R)d.f[1].im), f2 = mkc<R>((R)d.f[2].re, (R)d.f[2].im);
+  const M3<R> H = m_adj(GE);  // G_E^dag
+  // M = a1 Q + a2 Q^2 + f1 H + f2 (Q H + H Q)
+  M3<R> M = m_add(mul_nn(Qf, H), mul_nn(H, Qf));
+  M = m_scale(M, f2);
+  m_addto(M, m_scale(H, f1));
+  m_addto(M, m_scale(Qf, mkc<R>((R)a1.re, (R)a1.im)));
+  m_addto(M, m_scale(Q2f, mkc<R>((R)a2.re, (R)a2.im)));
+  // G_Omega = TA(i M^dag)
+  const M3<R> GO = m_ta(m_scale(m_adj(M), mkc<R>(0, 1)));
+  // E = exp(iQ) and the local gradient E^dag G' + G_Omega^dag C
+  const M3<R> E = expiq_assemble(q, q2, mkc<R>((R)d.f[0].re, (R)d.f[0].im), f1, f2);
+  M3<R> Gl = mul_dn(E, Gpm);
+  mac_dn(Gl, GO, C);
+  st_m3<R>(Gout + off, V, Gl);
+  st_m3<R>(K + off, V, m_rscale(mul_nn(GO, Umu), rho));
+}
+
+template <typename R>
+__device__ __forceinline__ M3<R> ld(const V2<R>* __restrict__ F, long long V, int dir, int s) {
+  return ld_m3<R>(F + (long long)dir * 9 * V + s, V);
+}
+
+// G_alpha(y) += sum_{mu in dirs, mu != alpha} [ K_mu(y) U_a(y+mu) U_mu(y+a)^dag
+//                 + K_mu(y-mu)^dag U_a(y-mu) U_mu(y-mu+a) + U_mu(y) U_a(y+mu) K_mu(y+a)^dag
+//                 + U_mu(y-mu)^dag U_a(y-mu) K_mu(y-mu+a)
+//                 + U_mu(y-mu)^dag K_a(y-mu) U_mu(y-mu+a) + U_mu(y) K_a(y+mu) U_mu(y+a)^dag ]
+template <typename R>
+__global__ void __launch_bounds__(128) k_bwd_staple(const V2<R>* __restrict__ U, const V2<R>* __restrict__ K,
+                                                    V2<R>* __restrict__ G, GeomArgs g, unsigned dirs) {
+  const long long V = g.V;
+  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const int s = (int)sl;
+  const int a = blockIdx.y;
+  if (!((dirs >> a) & 1u)) return;
+  int c[4];
+  site_coords(g, s, c);
+  const int s_pa = nb_fwd(g, s, coord_of(c, a), a);
+  M3<R> acc = ld<R>(G, V, a, s);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    if (mu == a || !((dirs >> mu) & 1u)) continue;
+    const int s_pmu = nb_fwd(g, s, c[mu], mu);
+    const int s_mmu = nb_bwd(g, s, c[mu], mu);
+    const int s_mmu_pa = nb_bwd(g, s_pa, c[mu], mu);  // y - mu + a
+    {
+      // K_mu(y) U_a(y+mu) U_mu(y+a)^dag
+      const M3<R> t = mul_nd(ld<R>(U, V, a, s_pmu), ld<R>(U, V, mu, s_pa));
+      mac_nn(acc, ld<R>(K, V, mu, s), t);
+    }
+    {
+      // K_mu(y-mu)^dag U_a(y-mu) U_mu(y-mu+a)
+      const M3<R> t = mul_nn(ld<R>(U, V, a, s_mmu), ld<R>(U, V, mu, s_mmu_pa));
+      mac_dn(acc, ld<R>(K, V, mu, s_mmu), t);
+    }
+    {
+      // U_mu(y) U_a(y+mu) K_mu(y+a)^dag
+      const M3<R> t = mul_nn(ld<R>(U, V, mu, s), ld<R>(U, V, a, s_pmu));
+      mac_nd(acc, t, ld<R>(K, V, mu, s_pa));
+    }
+    {
+      // U_mu(y-mu)^dag U_a(y-mu) K_mu(y-mu+a)
+      const M3<R> t = mul_dn(ld<R>(U, V, mu, s_mmu), ld<R>(U, V, a, s_mmu));
+      mac_nn(acc, t, ld<R>(K, V, mu, s_mmu_pa));
+    }
+    {
+      // U_mu(y-mu)^dag K_a(y-mu) U_mu(y-mu+a)
+      const M3<R> t = mul_dn(ld<R>(U, V, mu, s_mmu), ld<R>(K, V, a, s_mmu));
+      mac_nn(acc, t, ld<R>(U, V, mu, s_mmu_pa));
+    }
+    {
+      // U_mu(y) K_a(y+mu) U_mu(y+a)^dag
+      const M3<R> t = mul_nn(ld<R>(U, V, mu, s), ld<R>(K, V, a, s_pmu));
+      mac_nd(acc, t, ld<R>(U, V, mu, s_pa));
+    }
+  }
+  st_m3<R>(G + (long long)a * 9 * V + s, V, acc);
+}
+
+// Wilson-action gradient G_mu(x) = -(beta/3) * (sum over all nu != mu of the staples).
+template <typename R>
+__global__ void __launch_bounds__(128) k_wilson_grad(const V2<R>* __restrict__ U, V2<R>* __restrict__ G, GeomArgs g,
+                                                     R mbeta3) {
+  const long long V = g.V;
+  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const int s = (int)sl;
+  const int mu = blockIdx.y;
+  int c[4];
+  site_coords(g, s, c);
+  st_m3<R>(G + (long long)mu * 9 * V + s, V, m_rscale(staple_sum<R>(U, g, s, c, mu, 15u), mbeta3));
+}
+
+// F_mu(x) = TA(G_mu(x) U_mu(x)^dag)
+template <typename R>
+__global__ void k_force(const V2<R>* __restrict__ U, const V2<R>* __restrict__ G, V2<R>* __restrict__ F, long long V) {
+  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const long long off = (long long)blockIdx.y * 9 * V + sl;
+  st_m3<R>(F + off, V, m_ta(mul_nd(ld_m3<R>(G + off, V), ld_m3<R>(U + off, V))));
+}
+
+struct Bufs {
+  std::vector<void*> own;
+  cudaStream_t s;
+  ~Bufs() {
+    for (void* p : own) scratch_free(p, s);
+  }
+};
+
+template <typename R>
+static lq_status backward_impl(const lq_field* thin, double rho, int n, unsigned dirs, const lq_field* seed, double beta,
+                               lq_field* force, lq_field* grad_out, int every, cudaStream_t s) {
+  const GeomArgs g = geom_args(thin->geom);
+  const long long V = g.V;
+  const size_t fb = thin->bytes;
+  Bufs b;
+  b.s = s;
+  auto alloc = [&](void** p) -> lq_status {
+    lq_status st = scratch_alloc(p, fb, s, "lq_stout_backward");
+    if (st == LQ_OK) b.own.push_back(*p);
+    return st;
+  };
+  lq_status st;
+  // checkpoints: ck[j] holds U^(j) for j % every == 0 (ck[0] is the thin field itself)
+  std::vector<void*> ck(n + 1, nullptr);
+  ck[0] = thin->ptr;
+  void *w0, *w1, *Ga, *Gb, *Kb;
+  if ((st = alloc(&w0)) || (st = alloc(&w1)) || (st = alloc(&Ga)) || (st = alloc(&Gb)) || (st = alloc(&Kb))) return st;
+  for (int j = every; j < n; j += every)
+    if ((st = alloc(&ck[j]))) return st;
+  TuneChoice tc = stout_default_choice(thin->prec);
+  // recomputed fields follow lq_stout_smear's default (FP32 links are re-projected)
+  const int reproject = thin->prec == LQ_F32 ? 1 : 0;
+  // forward: U^(j) from the nearest checkpoint at or below j, into dst
+  auto forward_to = [&](int j, void* dst) -> lq_status {
+    const int j0 = (j / every) * every;
+    lq_status st2 = cuda_check(cudaMemcpyAsync(dst, ck[j0], fb, cudaMemcpyDeviceToDevice, s), "lq_stout_backward copy");
+    if (st2 != LQ_OK) return st2;
+    return stout_run_steps(dst, w1, thin->geom, thin->prec, rho, j - j0, dirs, reproject, tc, s);
+  };
+  for (int j = every; j < n; j += every) {
+    if ((st = forward_to(j, ck[j]))) return st;
+  }
+  // seed at U^(n)
+  if (seed) {
+    if ((st = cuda_check(cudaMemcpyAsync(Ga, seed->ptr, fb, cudaMemcpyDeviceToDevice, s), "lq_stout_backward seed")))
+      return st;
+  } else {
+    void* Un = thin->ptr;
+    if (n > 0) {
+      if ((st = forward_to(n, w0))) return st;
+      Un = w0;
+    }
+    dim3 grid((unsigned)((V + 127) / 128), 4);
+    k_wilson_grad<R><<<grid, 128, 0, s>>>((const V2<R>*)Un, (V2<R>*)Ga, g, (R)(-beta / 3.0));
+    if ((st = launch_check("k_wilson_grad"))) return st;
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const void* Uj = ck[j];
+    if (!Uj) {
+      if ((st = forward_to(j, w0))) return st;
+      Uj = w0;
+    }
+    dim3 grid((unsigned)((V + 127) / 128), 4);
+    k_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g, (R)rho, dirs);
+    if ((st = launch_check("k_bwd_link"))) return st;
+    k_bwd_staple<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Kb, (V2<R>*)Gb, g, dirs);
+    if ((st = launch_check("k_bwd_staple"))) return st;
+    std::swap(Ga, Gb);
+  }
+  if (force) {
+    dim3 grid((unsigned)((V + 255) / 256), 4);
+    k_force<R><<<grid, 256, 0, s>>>((const V2<R>*)thin->ptr, (const V2<R>*)Ga, (V2<R>*)force->ptr, V);
+    if ((st = launch_check("k_force"))) return st;
+  }
+  if (grad_out)
+    if ((st = cuda_check(cudaMemcpyAsync(grad_out->ptr, Ga, fb, cudaMemcpyDeviceToDevice, s), "lq_stout_backward grad")))
+      return st;
+  return LQ_OK;
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+extern "C" lq_status lq_stout_backward(const lq_field* thin, double rho, int n_steps, unsigned dirs_mask,
+                                       const lq_field* grad_seed, double beta, lq_field* force_out, lq_field* grad_out,
+                                       const lq_backward_opts* opts, void* stream) {
+  clear_error();
+  lq_status st = check_links(thin, "lq_stout_backward");
+  if (st != LQ_OK) return st;
+  if ((st = check_dirs(dirs_mask, "lq_stout_backward")) != LQ_OK) return st;
+  if (!(rho >= 0.0) || rho > 1e6 || n_steps < 0 || !(beta == beta)) {
+    set_error("lq_stout_backward: rho must be finite >= 0, n_steps >= 0, beta finite");
+    return LQ_ERR_ARG;
+  }
+  if (!force_out && !grad_out) {
+    set_error("lq_stout_backward: neither force_out nor grad_out given");
+    return LQ_ERR_ARG;
+  }
+  const lq_field* outs[3] = {grad_seed, force_out, grad_out};
+  for (const lq_field* f : outs) {
+    if (!f) continue;
+    if (f->kind != LQ_LINKS || f->prec != thin->prec || !same_geom(f->geom, thin->geom)) {
+      set_error("lq_stout_backward: seed/force/grad fields must be LINKS of the thin field's geometry and precision");
+      return LQ_ERR_GEOM;
+    }
+    if (f->ptr == thin->ptr) {
+      set_error("lq_stout_backward: outputs must not alias the thin links");
+      return LQ_ERR_ARG;
+    }
+  }
+  int every = 1;
+  if (opts && opts->struct_size >= (int)sizeof(lq_backward_opts) && opts->checkpoint_every > 0)
+    every = opts->checkpoint_every;
+  cudaStream_t s = as_stream(stream);
+  if (thin->prec == LQ_F64)
+    return backward_impl<double>(thin, rho, n_steps, dirs_mask, grad_seed, beta, force_out, grad_out, every, s);
+  return backward_impl<float>(thin, rho, n_steps, dirs_mask, grad_seed, beta, force_out, grad_out, every, s);
+}

@@ -1,0 +1,292 @@
+// Batched stout smearing of many independent lattices of uneven sizes: one
+// persistent launch per step walks a device work list of (config, direction,
+// tile) items handed out by an atomic counter; the n-step sequence can be a
+// replayed CUDA graph.  Block size and sites per thread (the tile) come from
+// the auto-tuner (thread geometry of Winter, "Accelerating QDP++ using GPUs",
+// Sec. 4.4).  Per-link arithmetic is stout_link(), so every configuration's
+// result is bit-identical to a separate lq_stout_smear call.
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "lq_internal.h"
+#include "stout_core.cuh"
+
+namespace lq {
+
+struct BatchDesc {
+  GeomArgs g;
+  void* a;               // the caller's links
+  void* b;               // this config's slice of the workspace
+  long long item_begin;  // first work item of this config
+  int tiles_per_dir;
+  int pad;
+};
+
+struct MuList4 {
+  int mu[4];
+};
+
+template <typename R, bool REPRO>
+__global__ void __launch_bounds__(256) k_stout_batch(const BatchDesc* __restrict__ D, int n_cfg, long long n_items,
+                                                     unsigned long long* __restrict__ counter, int parity, R rho,
+                                                     unsigned dirs, int nsite, MuList4 ml) {
+  typedef typename vec2<R>::type V2;
+  __shared__ long long item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ULL);
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= n_items) return;
+    int lo = 0, hi = n_cfg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (D[mid].item_begin <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const GeomArgs g = D[lo].g;
+    const long long local = item - D[lo].item_begin;
+    const int tpd = D[lo].tiles_per_dir;
+    const int mu = ml.mu[(int)(local / tpd)];
+    const long long tile = local % tpd;
+    const V2* in = (const V2*)(parity ? D[lo].b : D[lo].a);
+    V2* out = (V2*)(parity ? D[lo].a : D[lo].b);
+    const long long V = g.V;
+    for (int k = 0; k < nsite; ++k) {
+      const long long sl = (tile * nsite + k) * blockDim.x + threadIdx.x;
+      if (sl >= V) break;
+      const int s = (int)sl;
+      int c[4];
+      site_coords(g, s, c);
+      const M3<R> Up = stout_link<R>(in, g, s, c, mu, dirs, rho, REPRO);
+      st_m3<R>(out + (long long)mu * 9 * V + s, V, Up);
+    }
+  }
+}
+
+struct BatchPlan {
+  std::vector<BatchDesc> host;
+  BatchDesc* dev = nullptr;
+  unsigned long long* counters = nullptr;  // one per step
+  void* work = nullptr;
+  long long n_items = 0;
+  int n_steps = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+
+struct BatchKey {
+  std::vector<void*> ptrs;
+  std::vector<int> dims;
+  int prec, n, reproject, block, nsite, device, graph;
+  unsigned dirs;
+  double rho;
+  bool operator<(const BatchKey& o) const {
+    if (ptrs != o.ptrs) return ptrs < o.ptrs;
+    if (dims != o.dims) return dims < o.dims;
+    const int a[7] = {prec, n, reproject, block, nsite, device, graph};
+    const int b[7] = {o.prec, o.n, o.reproject, o.block, o.nsite, o.device, o.graph};
+    for (int i = 0; i < 7; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    if (dirs != o.dirs) return dirs < o.dirs;
+    return rho < o.rho;
+  }
+};
+
+static std::mutex g_batch_mu;
+static std::map<BatchKey, BatchPlan>& batch_cache() {
+  static std::map<BatchKey, BatchPlan> m;
+  return m;
+}
+static void free_plan(BatchPlan& p) {
+  if (p.exec) cudaGraphExecDestroy(p.exec);
+  if (p.dev) cudaFree(p.dev);
+  if (p.counters) cudaFree(p.counters);
+  if (p.work) cudaFree(p.work);
+  p = BatchPlan();
+}
+static void release_batch() {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (auto& kv : batch_cache()) free_plan(kv.second);
+  batch_cache().clear();
+}
+
+// Records the whole n-step sequence on stream s (also used under capture).
+static lq_status batch_sequence(lq_field* const* links, int n_cfg, const BatchPlan& p, double rho, unsigned dirs,
+                                int reproject, const TuneChoice& tc, int prec, cudaStream_t s) {
+  lq_status st = cuda_check(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.n_steps, s), "batch counters");
+  if (st) return st;
+  const size_t eb = elem_bytes(LQ_LINKS, prec);
+  for (int i = 0; i < n_cfg; ++i) {
+    const size_t db = (size_t)links[i]->geom.volume * 9 * eb;
+    for (int mu = 0; mu < 4; ++mu)
+      if (!((dirs >> mu) & 1u))
+        if ((st = cuda_check(cudaMemcpyAsync((char*)p.host[i].b + mu * db, (const char*)links[i]->ptr + mu * db, db,
+                                             cudaMemcpyDeviceToDevice, s),
+                             "batch pass-through copy")))
+          return st;
+  }
+  int nd = 0;
+  MuList4 ml;
+  for (int mu = 0; mu < 4; ++mu)
+    if ((dirs >> mu) & 1u) ml.mu[nd++] = mu;
+  for (int j = nd; j < 4; ++j) ml.mu[j] = 0;
+  const int grid = device_sm_count() * (prec == LQ_F64 ? 4 : 8) * 128 / tc.block;
+  for (int k = 0; k < p.n_steps; ++k) {
+    const int parity = k & 1;
+    unsigned long long* ctr = p.counters + k;
+    if (prec == LQ_F64) {
+      if (reproject)
+        k_stout_batch<double, true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, ml);
+      else
+        k_stout_batch<double, false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, ml);
+    } else {
+      if (reproject)
+        k_stout_batch<float, true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, ml);
+      else
+        k_stout_batch<float, false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, ml);
+    }
+    if ((st = launch_check("k_stout_batch"))) return st;
+  }
+  if (p.n_steps % 2 == 1) {
+    for (int i = 0; i < n_cfg; ++i) {
+      const size_t db = (size_t)links[i]->geom.volume * 9 * eb;
+      for (int mu = 0; mu < 4; ++mu)
+        if ((dirs >> mu) & 1u)
+          if ((st = cuda_check(cudaMemcpyAsync((char*)links[i]->ptr + mu * db, (const char*)p.host[i].b + mu * db, db,
+                                               cudaMemcpyDeviceToDevice, s),
+                               "batch result copy")))
+            return st;
+    }
+  }
+  return LQ_OK;
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+extern "C" lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, int n_steps, unsigned dirs_mask,
+                                          const lq_stout_opts* opts, void* stream) {
+  clear_error();
+  if (!links || n_cfg < 1) {
+    set_error("lq_stout_smear_batch: need n_cfg >= 1 fields");
+    return LQ_ERR_ARG;
+  }
+  lq_status st;
+  if ((st = check_dirs(dirs_mask, "lq_stout_smear_batch"))) return st;
+  if (!(rho >= 0.0) || rho > 1e6 || n_steps < 0) {
+    set_error("lq_stout_smear_batch: rho must be finite >= 0 and n_steps >= 0");
+    return LQ_ERR_ARG;
+  }
+  for (int i = 0; i < n_cfg; ++i) {
+    if ((st = check_links(links[i], "lq_stout_smear_batch"))) return st;
+    if (links[i]->prec != links[0]->prec) {
+      set_error("lq_stout_smear_batch: all fields must share one precision");
+      return LQ_ERR_GEOM;
+    }
+    for (int j = 0; j < i; ++j)
+      if (links[j]->ptr == links[i]->ptr) {
+        set_error("lq_stout_smear_batch: fields %d and %d alias", j, i);
+        return LQ_ERR_ARG;
+      }
+  }
+  const lq_stout_opts* o = (opts && opts->struct_size >= (int)sizeof(lq_stout_opts)) ? opts : nullptr;
+  if (n_steps == 0) return LQ_OK;
+  const int prec = links[0]->prec;
+  const int reproject = (o && o->reproject >= 0) ? o->reproject : (prec == LQ_F32 ? 1 : 0);
+  cudaStream_t s = as_stream(stream);
+  TuneChoice tc = stout_default_choice(prec);
+  if (o && o->block > 0) {
+    if (o->block % 32 != 0 || o->block > 256) {
+      set_error("lq_stout_smear_batch: block must be a multiple of 32 in [32, 256]");
+      return LQ_ERR_ARG;
+    }
+    tc.block = o->block;
+    tc.nsite = o->sites_per_thread > 0 ? o->sites_per_thread : 1;
+  } else if (tune_enabled()) {
+    // the tile shape tuned for the largest member is used for the whole batch
+    int big = 0;
+    for (int i = 1; i < n_cfg; ++i)
+      if (links[i]->geom.volume > links[big]->geom.volume) big = i;
+    if ((st = stout_choose(links[big], rho, dirs_mask, reproject, nullptr, s, &tc))) return st;
+  }
+  const bool use_graph = o && o->use_graph;
+  register_cache_release(release_batch);
+
+  BatchKey key;
+  for (int i = 0; i < n_cfg; ++i) {
+    key.ptrs.push_back(links[i]->ptr);
+    for (int d = 0; d < 4; ++d) key.dims.push_back(links[i]->geom.dims[d]);
+  }
+  key.prec = prec;
+  key.n = n_steps;
+  key.reproject = reproject;
+  key.block = tc.block;
+  key.nsite = tc.nsite;
+  key.device = current_device();
+  key.graph = use_graph ? 1 : 0;
+  key.dirs = dirs_mask;
+  key.rho = rho;
+
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  auto it = batch_cache().find(key);
+  if (it == batch_cache().end()) {
+    BatchPlan p;
+    p.n_steps = n_steps;
+    int nd = 0;
+    for (int mu = 0; mu < 4; ++mu) nd += (dirs_mask >> mu) & 1u;
+    size_t total = 0;
+    for (int i = 0; i < n_cfg; ++i) total += links[i]->bytes;
+    if ((st = cuda_check(cudaMalloc(&p.work, total), "batch workspace"))) return st;
+    size_t off = 0;
+    long long items = 0;
+    const long long tile = (long long)tc.block * tc.nsite;
+    for (int i = 0; i < n_cfg; ++i) {
+      BatchDesc d;
+      std::memset(&d, 0, sizeof(d));
+      d.g = geom_args(links[i]->geom);
+      d.a = links[i]->ptr;
+      d.b = (char*)p.work + off;
+      d.item_begin = items;
+      d.tiles_per_dir = (int)((d.g.V + tile - 1) / tile);
+      items += (long long)d.tiles_per_dir * nd;
+      off += links[i]->bytes;
+      p.host.push_back(d);
+    }
+    p.n_items = items;
+    if ((st = cuda_check(cudaMalloc(&p.dev, sizeof(BatchDesc) * n_cfg), "batch descriptors")) ||
+        (st = cuda_check(cudaMalloc(&p.counters, sizeof(unsigned long long) * n_steps), "batch counters")) ||
+        (st = cuda_check(cudaMemcpy(p.dev, p.host.data(), sizeof(BatchDesc) * n_cfg, cudaMemcpyHostToDevice),
+                         "batch descriptor upload"))) {
+      free_plan(p);
+      return st;
+    }
+    if (use_graph) {
+      cudaStream_t cap;
+      if ((st = cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "batch graph stream"))) {
+        free_plan(p);
+        return st;
+      }
+      cudaGraph_t graph = nullptr;
+      st = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "batch graph capture");
+      if (!st) {
+        lq_status st_run = batch_sequence(links, n_cfg, p, rho, dirs_mask, reproject, tc, prec, cap);
+        lq_status st_end = cuda_check(cudaStreamEndCapture(cap, &graph), "batch graph end capture");
+        st = st_run ? st_run : st_end;
+      }
+      if (!st) st = cuda_check(cudaGraphInstantiate(&p.exec, graph, 0), "batch graph instantiate");
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cap);
+      if (st) {
+        free_plan(p);
+        return st;
+      }
+    }
+    it = batch_cache().emplace(key, p).first;
+  }
+  const BatchPlan& p = it->second;
+  if (use_graph) return cuda_check(cudaGraphLaunch(p.exec, s), "batch graph launch");
+  return batch_sequence(links, n_cfg, p, rho, dirs_mask, reproject, tc, prec, s);
+}

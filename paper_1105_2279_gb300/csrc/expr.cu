@@ -23,7 +23,8 @@ __global__ void k_shift(const E* __restrict__ in, E* __restrict__ out, GeomArgs 
     const int s = (int)sl;
     int c[4];
     site_coords(g, s, c);
-    const int src = sign > 0 ? nb_fwd(g, s, c[mu], mu) : nb_bwd(g, s, c[mu], mu);
+    const int cm = coord_of(c, mu);
+    const int src = sign > 0 ? nb_fwd(g, s, cm, mu) : nb_bwd(g, s, cm, mu);
     for (int p = 0; p < planes; ++p) out[(long long)p * V + s] = __ldg(in + (long long)p * V + src);
   }
 }
@@ -106,8 +107,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_expr(DevProg prog, GeomArgs 
       switch (op.code) {
         case LQ_OP_LOAD: {
           int site = s;
-          if (op.sign > 0) site = nb_fwd(g, s, c[op.mu], op.mu);
-          if (op.sign < 0) site = nb_bwd(g, s, c[op.mu], op.mu);
+          if (op.sign > 0) site = nb_fwd(g, s, coord_of(c, op.mu), op.mu);
+          if (op.sign < 0) site = nb_bwd(g, s, coord_of(c, op.mu), op.mu);
           reg[op.dst] = load_operand<R>(prog.operand[op.a], prog.operand_kind[op.a], op.dir, V, site);
           break;
         }

@@ -19,15 +19,19 @@ struct MuList {
 
 // Variant 1: one thread per (site, mu) for N_site sites; neighbour links are
 // read through the read-only data path (L1 / L2 serve the ~19x reuse of each
-// link by neighbouring staples).
+// link by neighbouring staples).  Consecutive blocks take the smeared
+// directions of one site block, so the four sweeps share cached lines and
+// the field streams from DRAM about once per step.
 template <typename R, bool REPRO>
 __global__ void __launch_bounds__(256) k_stout_global(const typename vec2<R>::type* __restrict__ Uin,
                                                       typename vec2<R>::type* __restrict__ Uout, GeomArgs g,
-                                                      R rho, unsigned dirs, int nsite, MuList ml) {
-  const int mu = ml.mu[blockIdx.y];
+                                                      R rho, unsigned dirs, int nsite, int nd, MuList ml) {
+  const int mi = blockIdx.x % nd;
+  const long long sb = blockIdx.x / nd;
+  const int mu = mi == 0 ? ml.mu[0] : (mi == 1 ? ml.mu[1] : (mi == 2 ? ml.mu[2] : ml.mu[3]));
   const long long V = g.V;
   for (int k = 0; k < nsite; ++k) {
-    const long long sl = ((long long)blockIdx.x * nsite + k) * blockDim.x + threadIdx.x;
+    const long long sl = (sb * nsite + k) * blockDim.x + threadIdx.x;
     if (sl >= V) return;
     const int s = (int)sl;
     int c[4];
@@ -55,17 +59,17 @@ static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int
   const int block = tc.block > 0 ? tc.block : 128;
   const int nsite = tc.nsite > 0 ? tc.nsite : 1;
   const long long per_block = (long long)block * nsite;
-  dim3 grid((unsigned)((g.V + per_block - 1) / per_block), (unsigned)nd);
+  dim3 grid((unsigned)(((g.V + per_block - 1) / per_block) * nd));
   if (prec == LQ_F64) {
     if (reproject)
-      k_stout_global<double, true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, ml);
+      k_stout_global<double, true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml);
     else
-      k_stout_global<double, false><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, ml);
+      k_stout_global<double, false><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml);
   } else {
     if (reproject)
-      k_stout_global<float, true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, ml);
+      k_stout_global<float, true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd, ml);
     else
-      k_stout_global<float, false><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, ml);
+      k_stout_global<float, false><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd, ml);
   }
   return launch_check("stout step kernel");
 }

@@ -19,6 +19,10 @@ __device__ __forceinline__ void site_coords(const GeomArgs& g, int s, int c[4]) 
   c[2] = r % g.L[2];
   c[3] = r / g.L[2];
 }
+// c[mu] for a run-time mu without indexing a local array
+__device__ __forceinline__ int coord_of(const int c[4], int mu) {
+  return mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+}
 // site of x + nu, where x has coordinate c_nu along nu
 __device__ __forceinline__ int nb_fwd(const GeomArgs& g, int s, int c_nu, int nu) {
   return (c_nu + 1 < g.L[nu]) ? s + g.stride[nu] : s - (g.L[nu] - 1) * g.stride[nu];
@@ -42,7 +46,7 @@ __device__ __forceinline__ M3<R> staple_sum(const typename vec2<R>::type* __rest
   const long long V = g.V;
   M3<R> C;
   m_zero(C);
-  const int s_pmu = nb_fwd(g, s, c[mu], mu);
+  const int s_pmu = nb_fwd(g, s, coord_of(c, mu), mu);
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu || !((dirs >> nu) & 1u)) continue;
@@ -167,6 +171,109 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
     f.f2 = cconj(f.f2);
   }
   return f;
+}
+
+// f_j and their derivatives b1_j = df_j/dc1, b2_j = df_j/dc0 (FP64), for the
+// stout force (Morningstar & Peardon 2004, Sec. IV).  With c1 = 3u^2 + w^2,
+// c0 = 2u(u^2 - w^2) and D = 9u^2 - w^2 the chain rule through (u, w) gives
+//   b1_j = [2u r1_j + (3u^2 - w^2) r2_j - 2(15u^2 + w^2) f_j] / (2 D^2)
+//   b2_j = [r1_j - 3u r2_j - 24u f_j] / (2 D^2)
+// with r1_j = dh_j/du and r2_j = (1/w) dh_j/dw, xi1(w) = cos w/w^2 - sin w/w^3.
+struct CHDeriv {
+  cx<double> f[3], b1[3], b2[3];
+};
+__device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, double d2, cx<double> o01,
+                                                         cx<double> o02, cx<double> o12) {
+  CHDeriv r;
+  const double tq = (d0 + d1 + d2) * (1.0 / 3.0);
+  d0 -= tq;
+  d1 -= tq;
+  d2 -= tq;
+  const double n01 = cnorm2(o01), n02 = cnorm2(o02), n12 = cnorm2(o12);
+  const double c1 = 0.5 * (d0 * d0 + d1 * d1 + d2 * d2) + n01 + n02 + n12;
+  const cx<double> p = cmul(o01, o12);
+  const double re3 = p.re * o02.re + p.im * o02.im;
+  const double c0 = d0 * d1 * d2 - d0 * n12 - d1 * n02 - d2 * n01 + 2.0 * re3;
+  if (!(c1 >= LQ_C1_SERIES)) {
+    // Q -> 0: exp(iQ) = 1 + iQ - Q^2/2 - iQ^3/6 + Q^4/24 + iQ^5/120 ... reduced
+    // with Q^3 = c1 Q + c0 gives these first derivatives at Q = 0.
+    r.f[0] = mkc(1.0, 0.0);
+    r.f[1] = mkc(0.0, 1.0);
+    r.f[2] = mkc(-0.5, 0.0);
+    r.b1[0] = mkc(0.0, 0.0);
+    r.b1[1] = mkc(0.0, -1.0 / 6.0);
+    r.b1[2] = mkc(1.0 / 24.0, 0.0);
+    r.b2[0] = mkc(0.0, -1.0 / 6.0);
+    r.b2[1] = mkc(1.0 / 24.0, 0.0);
+    r.b2[2] = mkc(0.0, 1.0 / 120.0);
+    return r;
+  }
+  const bool neg = c0 < 0.0;
+  const double s3 = sqrt(c1 * (1.0 / 3.0));
+  const double c0max = 2.0 * s3 * s3 * s3;
+  const double x = fmin(fabs(c0) / c0max, 1.0);
+  const double theta = acos(x);
+  double st, ct;
+  sincos(theta * (1.0 / 3.0), &st, &ct);
+  const double u = s3 * ct;
+  const double w = sqrt(c1) * st;
+  const double u2 = u * u, w2 = w * w;
+  double sw, cw;
+  sincos(w, &sw, &cw);
+  double xi0, xi1;
+  if (fabs(w) <= LQ_XI0_SERIES) {
+    xi0 = 1.0 - w2 * (1.0 / 6.0) * (1.0 - w2 * (1.0 / 20.0) * (1.0 - w2 * (1.0 / 42.0)));
+    xi1 = -1.0 / 3.0 + w2 * (1.0 / 30.0) * (1.0 - w2 * (1.0 / 28.0) * (1.0 - w2 * (1.0 / 54.0)));
+  } else {
+    xi0 = sw / w;
+    xi1 = (cw - xi0) / w2;
+  }
+  double su, cu;
+  sincos(u, &su, &cu);
+  const cx<double> emiu = mkc(cu, -su);
+  const cx<double> e2iu = mkc(cu * cu - su * su, 2.0 * su * cu);
+  const cx<double> I = mkc(0.0, 1.0);
+  cx<double> h[3], r1[3], r2[3];
+  h[0] = cadd(cscale(e2iu, u2 - w2), cmul(emiu, mkc(8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0)));
+  h[1] = csub(cscale(e2iu, 2.0 * u), cmul(emiu, mkc(2.0 * u * cw, -(3.0 * u2 - w2) * xi0)));
+  h[2] = csub(e2iu, cmul(emiu, mkc(cw, 3.0 * u * xi0)));
+  // r1_0 = 2(u + i(u^2 - w^2)) e^{2iu} + 2 e^{-iu} [4u(2 - iu) cos w + (u(3u^2 + w^2) + i(9u^2 + w^2)) xi0]
+  r1[0] = cadd(cmul(mkc(2.0 * u, 2.0 * (u2 - w2)), e2iu),
+               cscale(cmul(emiu, mkc(8.0 * u * cw + u * (3.0 * u2 + w2) * xi0,
+                                     -4.0 * u2 * cw + (9.0 * u2 + w2) * xi0)), 2.0));
+  // r1_1 = 2(1 + 2iu) e^{2iu} + e^{-iu} [-2(1 - iu) cos w + (3u^2 - w^2 + 6iu) xi0]
+  r1[1] = cadd(cmul(mkc(2.0, 4.0 * u), e2iu),
+               cmul(emiu, mkc(-2.0 * cw + (3.0 * u2 - w2) * xi0, 2.0 * u * cw + 6.0 * u * xi0)));
+  // r1_2 = 2i e^{2iu} + i e^{-iu} [cos w - 3(1 - iu) xi0]
+  r1[2] = cadd(cmul(mkc(0.0, 2.0), e2iu), cmul(I, cmul(emiu, mkc(cw - 3.0 * xi0, 3.0 * u * xi0))));
+  // r2_0 = -2 e^{2iu} + 2iu e^{-iu} [cos w + (1 + 4iu) xi0 + 3u^2 xi1]
+  r2[0] = cadd(cscale(e2iu, -2.0),
+               cmul(mkc(0.0, 2.0 * u), cmul(emiu, mkc(cw + xi0 + 3.0 * u2 * xi1, 4.0 * u * xi0))));
+  // r2_1 = -i e^{-iu} [cos w + (1 + 2iu) xi0 - 3u^2 xi1]
+  r2[1] = cmul(mkc(0.0, -1.0), cmul(emiu, mkc(cw + xi0 - 3.0 * u2 * xi1, 2.0 * u * xi0)));
+  // r2_2 = e^{-iu} [xi0 - 3iu xi1]
+  r2[2] = cmul(emiu, mkc(xi0, -3.0 * u * xi1));
+  const double D = 9.0 * u2 - w2;
+  const double inv = 1.0 / D;
+  const double inv2 = 0.5 * inv * inv;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    r.f[j] = cscale(h[j], inv);
+    r.b1[j] = cscale(csub(cadd(cscale(r1[j], 2.0 * u), cscale(r2[j], 3.0 * u2 - w2)),
+                          cscale(r.f[j], 2.0 * (15.0 * u2 + w2))),
+                     inv2);
+    r.b2[j] = cscale(csub(csub(r1[j], cscale(r2[j], 3.0 * u)), cscale(r.f[j], 24.0 * u)), inv2);
+  }
+  if (neg) {  // f_j -> (-1)^j conj f_j,  b_ij -> (-1)^(i+j+1) conj b_ij
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double sf = (j % 2 == 0) ? 1.0 : -1.0;
+      r.f[j] = cscale(cconj(r.f[j]), sf);
+      r.b1[j] = cscale(cconj(r.b1[j]), sf);
+      r.b2[j] = cscale(cconj(r.b2[j]), -sf);
+    }
+  }
+  return r;
 }
 
 // exp(iQ) = f0 + f1 Q + f2 Q^2 as a full matrix.

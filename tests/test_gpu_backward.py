@@ -1,0 +1,147 @@
+"""GPU stout force (lq_stout_backward) vs the oracle's reverse-mode gradient
+and vs central finite differences of the GPU forward.
+
+FP64: max |F_gpu - F_oracle| <= 1e-11 * max |F_oracle| (the recursion sums
+~10^3 terms of size |F| per link; rounding ~1e-16 each).  FP32 (FP32 matrix
+algebra, FP64 coefficients): <= 2e-5 * max |F| per step.
+"""
+import numpy as np
+import pytest
+
+import fieldgen
+import paper_1105_2279_gb300 as lq
+from oracle import backward, gauge, lattice, stout
+from oracle.su3 import adj
+from tests.gpu_util import upload_links
+
+pytestmark = pytest.mark.gpu
+ALL, SPATIAL = (0, 1, 2, 3), (0, 1, 2)
+
+
+def gpu_force(U, prec, rho, n, dirs, beta=6.0, seed=None, every=1):
+    f = upload_links(U, prec)
+    F = lq.Field(f.geom, lq.LQ_LINKS, prec)
+    G = lq.Field(f.geom, lq.LQ_LINKS, prec)
+    s = upload_links(seed, prec) if seed is not None else None
+    lq.stout_backward(f, rho, n, dirs, F, grad_seed=s, beta=beta, grad_out=G, checkpoint_every=every)
+    return F.download(), G.download()
+
+
+@pytest.mark.parametrize("dims,gen,rho,n,dirs,every", [
+    ((3, 4, 3, 4), "near", 0.1, 0, ALL, 1),
+    ((3, 4, 3, 4), "near", 0.1, 1, ALL, 1),
+    ((4, 3, 4, 3), "haar", 0.1, 2, ALL, 1),
+    ((4, 3, 4, 3), "near", 0.125, 3, ALL, 2),
+    ((3, 4, 5, 3), "near", 0.1, 3, SPATIAL, 1),
+    ((4, 4, 3, 3), "haar", 0.2, 2, (0, 3), 3),
+    ((2, 2, 2, 2), "near", 0.1, 2, ALL, 1),
+])
+def test_force_f64_matches_oracle(gpu, dims, gen, rho, n, dirs, every):
+    U = fieldgen.haar_su3(dims, 300) if gen == "haar" else fieldgen.near_identity_su3(dims, 300)
+    F_ref, G_ref = backward.smeared_wilson_force(U, rho, n, dirs, 6.0)
+    F, G = gpu_force(U, lq.LQ_F64, rho, n, dirs, every=every)
+    scale = np.max(np.abs(F_ref))
+    assert np.max(np.abs(F - F_ref)) <= 1e-11 * scale
+    assert np.max(np.abs(G - G_ref)) <= 1e-11 * np.max(np.abs(G_ref))
+
+
+def test_force_with_given_seed(gpu):
+    dims = (3, 4, 3, 4)
+    U = fieldgen.near_identity_su3(dims, 301)
+    seed = fieldgen.haar_su3(dims, 302) * 0.7      # any complex field works as dS/dU^(n)
+    G_ref = backward.stout_backward(U, 0.1, 2, ALL, seed)
+    _, G = gpu_force(U, lq.LQ_F64, 0.1, 2, ALL, seed=seed)
+    assert np.max(np.abs(G - G_ref)) <= 1e-11 * np.max(np.abs(G_ref))
+
+
+@pytest.mark.parametrize("n,dirs", [(1, ALL), (2, SPATIAL)])
+def test_force_f32(gpu, n, dirs):
+    dims = (4, 3, 4, 3)
+    U = fieldgen.near_identity_su3(dims, 303)
+    F_ref, _ = backward.smeared_wilson_force(U, 0.1, n, dirs, 6.0)
+    F, _ = gpu_force(U, lq.LQ_F32, 0.1, n, dirs)
+    assert np.max(np.abs(F.astype(np.complex128) - F_ref)) <= 2e-5 * max(1, n) * np.max(np.abs(F_ref))
+
+
+def test_autograd_chain_matches_oracle(gpu):
+    import torch
+    dims = (3, 4, 3, 4)
+    U = fieldgen.near_identity_su3(dims, 304)
+    f = upload_links(U, lq.LQ_F64)
+    t = f.tensor.clone().requires_grad_(True)
+    S = lq.wilson_action_autograd(lq.stout_smear_autograd(t, dims, 0.1, 2, ALL), dims, 6.0)
+    S.backward()
+    assert abs(S.item() - gauge.wilson_action(stout.stout_smear(U, 0.1, 2, ALL), 6.0)) < 1e-10
+    # tensor gradient [dir][comp][site][re/im] -> complex AoS
+    g = t.grad.cpu().numpy()
+    G = (g[..., 0] + 1j * g[..., 1]).transpose(2, 0, 1).reshape(lattice.field_shape(dims) + (4, 3, 3))
+    _, G_ref = backward.smeared_wilson_force(U, 0.1, 2, ALL, 6.0)
+    assert np.max(np.abs(G - G_ref)) <= 1e-11 * np.max(np.abs(G_ref))
+
+
+def _plane_diff_programs():
+    """Per plane: Re tr P(operand 0) - Re tr P(operand 1), summed per site before reduction."""
+    progs = []
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            p = []
+            for k, r0 in ((0, 0), (1, 4)):
+                p += [("loadl", r0, k, mu, 0, 0), ("loadl", r0 + 1, k, nu, mu, +1), ("mul", r0, r0, r0 + 1),
+                      ("loadl", r0 + 1, k, nu, 0, 0), ("loadl", r0 + 2, k, mu, nu, +1),
+                      ("mul", r0 + 1, r0 + 1, r0 + 2), ("adj", r0 + 1, r0 + 1), ("mul", r0, r0, r0 + 1),
+                      ("retr", r0, r0)]
+            p += [("sub", 0, 0, 4), ("store", 0)]
+            progs.append(p)
+    return progs
+
+
+def test_24c48_three_steps_fd_and_oracle(gpu):
+    """24^3 x 48, exp(i 0.3 H) links, 3 steps rho = 0.1 in 4 dims, Wilson action
+    beta = 6 of the smeared field: the FP64 GPU force against central finite
+    differences (step 1e-6 along random unit su(3) directions at 32 random
+    links; the action difference is formed per site before summation) and
+    against the oracle gradient at one link (periodic box of side 15: the
+    force at a link depends on links at most 2n+1 = 7 sites away)."""
+    from scipy.linalg import expm
+    dims = (24, 24, 24, 48)
+    n, rho, beta, eps = 3, 0.1, 6.0, 1e-6
+    U = fieldgen.near_identity_su3(dims, 4)
+    F, _ = gpu_force(U, lq.LQ_F64, rho, n, ALL, beta=beta, every=2)
+    g = lq.Geometry(dims)
+    fp, fm = lq.Field(g, lq.LQ_LINKS, lq.LQ_F64), lq.Field(g, lq.LQ_LINKS, lq.LQ_F64)
+    progs = _plane_diff_programs()
+    rng = np.random.default_rng(44)
+    worst = 0.0
+    for _ in range(32):
+        mu = int(rng.integers(4))
+        x = tuple(int(rng.integers(L)) for L in lattice.field_shape(dims))
+        X = fieldgen.su3_direction(rng)
+        up, dn = U.copy(), U.copy()
+        up[x + (mu,)] = expm(eps * X) @ U[x + (mu,)]
+        dn[x + (mu,)] = expm(-eps * X) @ U[x + (mu,)]
+        fp.upload(up)
+        fm.upload(dn)
+        lq.stout_smear(fp, rho, n, ALL)
+        lq.stout_smear(fm, rho, n, ALL)
+        d_retr = sum(lq.expr_eval(p, [fp, fm], reduce=True).real for p in progs) / 3.0  # tr of the 1 * scalar
+        fd = -(beta / 3.0) * d_retr / (2 * eps)
+        an = float(np.real(np.trace(adj(F[x + (mu,)]) @ X)))
+        worst = max(worst, abs(fd - an) / max(1.0, abs(an)))
+    assert worst < 1e-7, worst
+    r = 2 * n + 1
+    for _ in range(1):
+        mu = int(rng.integers(4))
+        c = [int(rng.integers(L)) for L in dims]
+        box = lattice.sub_box(U, c, r)
+        Fb, _ = backward.smeared_wilson_force(box, rho, n, ALL, beta)
+        ref = Fb[r, r, r, r, mu]
+        got = F[c[3], c[2], c[1], c[0], mu]
+        assert np.max(np.abs(got - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_24c48_f32_force_vs_f64(gpu):
+    dims = (24, 24, 24, 48)
+    U = fieldgen.near_identity_su3(dims, 4)
+    F64, _ = gpu_force(U, lq.LQ_F64, 0.1, 3, ALL)
+    F32, _ = gpu_force(U, lq.LQ_F32, 0.1, 3, ALL)
+    assert np.max(np.abs(F32.astype(np.complex128) - F64)) <= 6e-5 * np.max(np.abs(F64))
