@@ -160,7 +160,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--f64-steps", type=int, default=3)
     ap.add_argument("--dims", default=None, help="Lx,Ly,Lz,Lt override (smaller profiling cases)")
+    ap.add_argument("--workload", default="stout48", choices=["stout48", "batch64", "backward24", "micro16"],
+                    help="stout48 (default, the headline line); the others print their own JSON line")
     args = ap.parse_args()
+    if args.workload != "stout48" and args.impl == "ours":
+        import bench_workloads
+        bench_workloads.run(args)
+        return
     global DIMS, WORKLOAD
     if args.dims:
         DIMS = tuple(int(x) for x in args.dims.split(","))

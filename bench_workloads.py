@@ -1,0 +1,129 @@
+"""Secondary benchmark workloads of bench.py (each prints one JSON line):
+
+* batch64    -- 64 independent lattices L^3 x 2L, L uniform in {8,12,16,20,24}
+                (seed 3), 6 spatial stout steps rho = 0.1, FP32 links with FP64
+                coefficients and re-projection: one persistent launch per step
+                replayed as a CUDA graph, vs the same persistent sequence
+                without a graph, vs one lq_stout_smear call per configuration.
+* backward24 -- 24^3 x 48, 3 stout steps rho = 0.1 in 4 dims, gradient of the
+                Wilson action (beta = 6) of the smeared field w.r.t. the thin
+                links, FP64 and FP32, every step checkpointed vs recomputed.
+* micro16    -- 16^3 x 32, 10 spatial steps rho = 0.1 in FP64, and the fused
+                expression micro-suite on the same field: sum_mu tr(U_mu(x)
+                U_mu(x+mu)), U_mu(x) U_nu(x+mu)^dag, plaquette.
+Inputs are resident on the device before timing; times are CUDA events.
+"""
+import json
+
+import numpy as np
+
+
+def _events(torch, fn, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _field(lq, fieldgen, dims, seed, prec, device="cuda"):
+    import torch
+    U = fieldgen.near_identity_su3_torch(dims, seed, device=device).cpu().numpy()
+    torch.cuda.empty_cache()
+    return lq.Field.from_host(lq.Geometry(dims), lq.LQ_LINKS, prec, U), U
+
+
+def batch64(args, torch, lq, fieldgen):
+    Ls = fieldgen.batch_sizes(3, 64)
+    fields = []
+    for i, L in enumerate(Ls):
+        f, _ = _field(lq, fieldgen, (L, L, L, 2 * L), 3 + i, lq.LQ_F32)
+        fields.append(f)
+    sites = sum(2 * L ** 4 for L in Ls)
+    links = 6 * sites * 3
+    dirs = (0, 1, 2)
+    t_graph = _events(torch, lambda: lq.stout_smear_batch(fields, 0.1, 6, dirs, use_graph=True), args.steps, args.warmup)
+    t_plain = _events(torch, lambda: lq.stout_smear_batch(fields, 0.1, 6, dirs), args.steps, args.warmup)
+
+    def separate():
+        for f in fields:
+            lq.stout_smear(f, 0.1, 6, dirs)
+    t_sep = _events(torch, separate, args.steps, args.warmup)
+    return {"metric": "stout link-updates/s (batch of 64 uneven lattices)", "value": links / (t_graph * 1e-3),
+            "unit": "link-updates/s", "ms_per_step": t_graph, "dtype": "f32",
+            "config": {"workload": "64 x L^3x2L, L in {8,12,16,20,24} seed 3, 6 spatial steps rho=0.1",
+                       "L": Ls, "sites": sites},
+            "persistent_no_graph": {"value": links / (t_plain * 1e-3), "ms_per_step": t_plain},
+            "separate_calls": {"value": links / (t_sep * 1e-3), "ms_per_step": t_sep,
+                               "launches_per_step": 64 * 6},
+            "speedup_vs_separate": t_sep / t_graph}
+
+
+def backward24(args, torch, lq, fieldgen):
+    dims = (24, 24, 24, 48)
+    V = int(np.prod(dims))
+    out = {"metric": "stout force link-updates/s (3 steps, Wilson action)", "unit": "link-updates/s",
+           "config": {"workload": "24^3x48, exp(i*0.3*H) links seed 4, 3 stout steps rho=0.1 in 4 dims, beta=6"}}
+    for name, prec in (("f64", lq.LQ_F64), ("f32", lq.LQ_F32)):
+        f, _ = _field(lq, fieldgen, dims, 4, prec)
+        F = lq.Field(f.geom, lq.LQ_LINKS, prec)
+        res = {}
+        for every in (1, 3):
+            t = _events(torch, lambda: lq.stout_backward(f, 0.1, 3, (0, 1, 2, 3), F, beta=6.0, checkpoint_every=every),
+                        args.steps, args.warmup)
+            res[f"checkpoint_every_{every}"] = {"ms": t, "value": 3 * V * 4 / (t * 1e-3)}
+        g = lq.Field(f.geom, lq.LQ_LINKS, prec)
+        g.tensor.copy_(f.tensor)
+        tf = _events(torch, lambda: lq.stout_smear(g, 0.1, 3, (0, 1, 2, 3)), args.steps, args.warmup)
+        res["forward_ms"] = tf
+        out[name] = res
+    out["value"] = out["f64"]["checkpoint_every_1"]["value"]
+    out["dtype"] = "f64"
+    return out
+
+
+def micro16(args, torch, lq, fieldgen):
+    dims = (16, 16, 16, 32)
+    V = int(np.prod(dims))
+    f, U = _field(lq, fieldgen, dims, 1, lq.LQ_F64)
+    g = lq.Field(f.geom, lq.LQ_LINKS, lq.LQ_F64)
+    g.tensor.copy_(f.tensor)
+    t_smear = _events(torch, lambda: lq.stout_smear(g, 0.1, 10, (0, 1, 2)), args.steps, args.warmup)
+    p_tr = []
+    for mu in range(4):
+        p_tr += [("loadl", 0, 0, mu, 0, 0), ("loadl", 1, 0, mu, mu, +1), ("mul", 2, 0, 1)]
+        p_tr += [("add", 3, 3, 2)] if mu else [("add", 3, 2, 2), ("sub", 3, 3, 2)]
+    p_tr += [("store", 3)]
+    p_adj = [("loadl", 0, 0, 0, 0, 0), ("loadl", 1, 0, 1, 0, +1), ("adj", 2, 1), ("mul", 3, 0, 2), ("store", 3)]
+    out = lq.Field(f.geom, lq.LQ_COLOR_MATRIX, lq.LQ_F64)
+    t_tr = _events(torch, lambda: lq.expr_eval(p_tr, [f], reduce=True), args.steps, args.warmup)
+    t_adj = _events(torch, lambda: lq.expr_eval(p_adj, [f], out=out), args.steps, args.warmup)
+    t_plaq = _events(torch, lambda: lq.plaquette(f), args.steps, args.warmup)
+    links = 10 * V * 3
+    return {"metric": "stout link-updates/s (16^3x32, 10 spatial steps, FP64)", "value": links / (t_smear * 1e-3),
+            "unit": "link-updates/s", "ms_per_step": t_smear, "dtype": "f64",
+            "config": {"workload": "16^3x32, exp(i*0.3*H) links seed 1, 10 stout steps rho=0.1 spatial"},
+            "micro_suite_ms": {"trace_sum_mu_tr_UU_shift": t_tr, "shifted_adjoint_product": t_adj,
+                               "plaquette": t_plaq},
+            "micro_suite_gb_s": {"trace_sum": V * 4 * 2 * 144 / (t_tr * 1e-3) / 1e9 / 2,
+                                 "shifted_adjoint_product": V * (2 * 144 + 144) / (t_adj * 1e-3) / 1e9}}
+
+
+def run(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import fieldgen
+    import paper_1105_2279_gb300 as lq
+    torch.cuda.set_device(0)
+    fn = {"batch64": batch64, "backward24": backward24, "micro16": micro16}[args.workload]
+    res = fn(args, torch, lq, fieldgen)
+    res.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                "data": "synthetic", "workload_mode": args.workload})
+    print(json.dumps(res), flush=True)

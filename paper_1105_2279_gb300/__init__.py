@@ -238,7 +238,8 @@ def stout_backward(thin, rho, n_steps, dirs, force_out, grad_seed=None, beta=6.0
     o.checkpoint_every = int(checkpoint_every)
     _check(L.load().lq_stout_backward(thin.handle, float(rho), int(n_steps), dirs_mask(dirs),
                                       grad_seed.handle if grad_seed is not None else None, float(beta),
-                                      force_out.handle, grad_out.handle if grad_out is not None else None,
+                                      force_out.handle if force_out is not None else None,
+                                      grad_out.handle if grad_out is not None else None,
                                       byref(o), _stream(stream)), "lq_stout_backward")
 
 

@@ -216,15 +216,20 @@ static lq_status backward_impl(const lq_field* thin, double rho, int n, unsigned
   TuneChoice tc = stout_default_choice(thin->prec);
   // recomputed fields follow lq_stout_smear's default (FP32 links are re-projected)
   const int reproject = thin->prec == LQ_F32 ? 1 : 0;
-  // forward: U^(j) from the nearest checkpoint at or below j, into dst
+  // forward: U^(j) from the nearest stored checkpoint at or below j (stored
+  // indices are multiples of `every` below n), into dst
   auto forward_to = [&](int j, void* dst) -> lq_status {
-    const int j0 = (j / every) * every;
+    int j0 = (j / every) * every;
+    if (j0 >= n) j0 = ((n - 1) / every) * every;
     lq_status st2 = cuda_check(cudaMemcpyAsync(dst, ck[j0], fb, cudaMemcpyDeviceToDevice, s), "lq_stout_backward copy");
     if (st2 != LQ_OK) return st2;
     return stout_run_steps(dst, w1, thin->geom, thin->prec, rho, j - j0, dirs, reproject, tc, s);
   };
-  for (int j = every; j < n; j += every) {
-    if ((st = forward_to(j, ck[j]))) return st;
+  for (int j = every; j < n; j += every) {  // ck[j] = `every` steps from ck[j - every]
+    if ((st = cuda_check(cudaMemcpyAsync(ck[j], ck[j - every], fb, cudaMemcpyDeviceToDevice, s),
+                         "lq_stout_backward checkpoint")))
+      return st;
+    if ((st = stout_run_steps(ck[j], w1, thin->geom, thin->prec, rho, every, dirs, reproject, tc, s))) return st;
   }
   // seed at U^(n)
   if (seed) {

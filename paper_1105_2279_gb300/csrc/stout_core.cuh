@@ -4,6 +4,7 @@
 // re-projection.  Shared by the single-lattice, batched and backward kernels.
 #pragma once
 
+#include "fp64_math.cuh"
 #include "lq_internal.h"
 #include "su3.cuh"
 
@@ -115,7 +116,11 @@ struct CHCoef {
 
 // Cayley-Hamilton coefficients of exp(iQ) = f0 + f1 Q + f2 Q^2, in FP64
 // (Morningstar & Peardon 2004, Sec. III).  The input Q is re-made exactly
-// traceless in FP64 first.
+// traceless in FP64 first.  The same quantities as the paper's formulas are
+// formed with few FP64 instructions (fp64_math.cuh):
+//   1/sqrt(c1/3) by Newton;  |c0|/c0max = |c0| (1/sqrt(c1/3))^3 / 2;
+//   cos(theta/3) as the root of 4y^3 - 3y = |c0|/c0max;  w^2 = c1 (1 - y^2);
+//   cos w and xi0(w) = sin(w)/w from w^2 by their series when w <= pi/4.
 __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d2, cx<double> o01,
                                                   cx<double> o02, cx<double> o12) {
   CHCoef f;
@@ -136,22 +141,25 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
     return f;
   }
   const bool neg = c0 < 0.0;
-  const double s3 = sqrt(c1 * (1.0 / 3.0));
-  const double c0max = 2.0 * s3 * s3 * s3;
-  const double x = fmin(fabs(c0) / c0max, 1.0);
-  const double theta = acos(x);
-  double st, ct;
-  sincos(theta * (1.0 / 3.0), &st, &ct);
-  const double u = s3 * ct;
-  const double w = sqrt(c1) * st;
-  const double u2 = u * u, w2 = w * w;
-  double sw, cw;
-  sincos(w, &sw, &cw);
-  const double xi0 = (fabs(w) <= LQ_XI0_SERIES)
-                         ? 1.0 - w2 * (1.0 / 6.0) * (1.0 - w2 * (1.0 / 20.0) * (1.0 - w2 * (1.0 / 42.0)))
-                         : sw / w;
+  const double a = c1 * (1.0 / 3.0);
+  const double r3 = rsqrt_nr(a);                                   // 1/sqrt(c1/3)
+  const double s3 = a * r3;                                        // sqrt(c1/3)
+  const double x = fmin(0.5 * fabs(c0) * (r3 * r3 * r3), 1.0);     // |c0| / c0max
+  const double y = cos_third_acos(x);                              // cos(theta/3)
+  const double u = s3 * y;
+  const double u2 = u * u;
+  const double w2 = fmax(c1 * ((1.0 - y) * (1.0 + y)), 0.0);       // w^2 = c1 sin^2(theta/3)
+  double cw, xi0;
+  if (w2 <= 0.61685027506808491) {                                 // w <= pi/4
+    cos_sinc_from_sq(w2, &cw, &xi0);
+  } else {
+    const double rw = rsqrt_nr(w2);
+    double sw;
+    sincos_red(w2 * rw, &sw, &cw);
+    xi0 = sw * rw;
+  }
   double su, cu;
-  sincos(u, &su, &cu);
+  sincos_red(u, &su, &cu);
   const cx<double> emiu = mkc(cu, -su);
   const cx<double> e2iu = mkc(cu * cu - su * su, 2.0 * su * cu);
   // h0 = (u^2 - w^2) e^{2iu} + e^{-iu} [8u^2 cos w + 2iu(3u^2 + w^2) xi0]
@@ -161,7 +169,7 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
   const cx<double> h1 = csub(cscale(e2iu, 2.0 * u), cmul(emiu, mkc(2.0 * u * cw, -(3.0 * u2 - w2) * xi0)));
   // h2 = e^{2iu} - e^{-iu} [cos w + 3iu xi0]
   const cx<double> h2 = csub(e2iu, cmul(emiu, mkc(cw, 3.0 * u * xi0)));
-  const double inv = 1.0 / (9.0 * u2 - w2);
+  const double inv = rcp_nr(9.0 * u2 - w2);   // 9u^2 - w^2 >= 2 c1 > 0
   f.f0 = cscale(h0, inv);
   f.f1 = cscale(h1, inv);
   f.f2 = cscale(h2, inv);
@@ -298,7 +306,7 @@ __device__ __forceinline__ void reproject_f64(M3<double>& m) {
   double n0 = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) n0 += cnorm2(m.e[k]);
-  const double r0 = rsqrt(n0);
+  const double r0 = rsqrt_nr(n0);
 #pragma unroll
   for (int k = 0; k < 3; ++k) m.e[k] = cscale(m.e[k], r0);
   cx<double> p = mkc(0.0, 0.0);
@@ -310,7 +318,7 @@ __device__ __forceinline__ void reproject_f64(M3<double>& m) {
     m.e[3 + k] = csub(m.e[3 + k], cmul(p, m.e[k]));
     n1 += cnorm2(m.e[3 + k]);
   }
-  const double r1 = rsqrt(n1);
+  const double r1 = rsqrt_nr(n1);
 #pragma unroll
   for (int k = 0; k < 3; ++k) m.e[3 + k] = cscale(m.e[3 + k], r1);
   // row2 = conj(row0 x row1)
@@ -325,6 +333,26 @@ template <typename A, typename B> __device__ __forceinline__ M3<A> m_convert(con
   for (int i = 0; i < 9; ++i) r.e[i] = mkc<A>((A)m.e[i].re, (A)m.e[i].im);
   return r;
 }
+// FP32 <-> FP64 element conversions on the integer pipe (fp64_math.cuh).
+__device__ __forceinline__ double to_f64(float x) { return f2d(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ float to_f32(double x) { return d2f(x); }
+template <typename R> __device__ __forceinline__ R from_f64(double x);
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return d2f(x); }
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+
+// Re-projects a link held in precision R through FP64 (rows 0 and 1 are
+// converted in, all three rows converted out).
+template <typename R> __device__ __forceinline__ M3<R> reproject_via_f64(const M3<R>& m) {
+  M3<double> d;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d.e[i] = mkc(to_f64(m.e[i].re), to_f64(m.e[i].im));
+  reproject_f64(d);
+  M3<R> r;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) r.e[i] = mkc<R>(from_f64<R>(d.e[i].re), from_f64<R>(d.e[i].im));
+  return r;
+}
 
 // New link U'_mu(x) for one (site, mu): FP64 coefficients always; matrix
 // algebra in R; optional FP64 re-projection.
@@ -336,18 +364,15 @@ __device__ __forceinline__ M3<R> stout_link(const typename vec2<R>::type* __rest
   const M3<R> Umu = ld_link<R>(U, g.V, mu, s);
   const M3<R> Om = mul_nd(C, Umu);
   const QH<R> q = q_from_omega(Om);
-  const CHCoef f = ch_coefficients((double)q.d0, (double)q.d1, (double)q.d2,
-                                   mkc<double>(q.o01.re, q.o01.im), mkc<double>(q.o02.re, q.o02.im),
-                                   mkc<double>(q.o12.re, q.o12.im));
+  const CHCoef f = ch_coefficients(to_f64(q.d0), to_f64(q.d1), to_f64(q.d2),
+                                   mkc(to_f64(q.o01.re), to_f64(q.o01.im)), mkc(to_f64(q.o02.re), to_f64(q.o02.im)),
+                                   mkc(to_f64(q.o12.re), to_f64(q.o12.im)));
   const QH<R> q2 = q_square(q);
-  const M3<R> E = expiq_assemble(q, q2, mkc<R>((R)f.f0.re, (R)f.f0.im), mkc<R>((R)f.f1.re, (R)f.f1.im),
-                                 mkc<R>((R)f.f2.re, (R)f.f2.im));
+  const M3<R> E = expiq_assemble(q, q2, mkc<R>(from_f64<R>(f.f0.re), from_f64<R>(f.f0.im)),
+                                 mkc<R>(from_f64<R>(f.f1.re), from_f64<R>(f.f1.im)),
+                                 mkc<R>(from_f64<R>(f.f2.re), from_f64<R>(f.f2.im)));
   M3<R> Up = mul_nn(E, Umu);
-  if (reproject) {
-    M3<double> d = m_convert<double, R>(Up);
-    reproject_f64(d);
-    Up = m_convert<R, double>(d);
-  }
+  if (reproject) Up = reproject_via_f64(Up);
   return Up;
 }
 
