@@ -224,6 +224,24 @@ lq_status lq_stout_backward(const lq_field* thin_links, double rho, int n_steps,
 lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, int n_steps,
                                unsigned dirs_mask, const lq_stout_opts* opts, void* stream);
 
+/* Stout smearing that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * allocate -- applications whose own allocator already holds all device
+ * memory, plug-ins whose host forbids device allocations, and latency-critical
+ * paths that must not risk an allocation's synchronisation or failure.
+ * Same arguments and results as lq_stout_smear with default options (FP32
+ * links re-projected, no graph), but the double buffer is a built-in device
+ * array of LQ_NOALLOC_WORK_BYTES (32 MiB) that every GPU loading the library
+ * holds until the process exits; fields needing more return LQ_ERR_ARG
+ * (FP64 up to 58,254 sites, FP32 up to 116,508 sites).  The first call on each
+ * device looks the array's device address up (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls whose work overlaps on the GPU (different streams, or different host
+ * threads on one device) race; serialise them.  The array keeps the last
+ * call's contents; nothing in it needs to start at zero. */
+#define LQ_NOALLOC_WORK_BYTES (32u * 1024u * 1024u)
+lq_status lq_stout_smear_noalloc(lq_field* links_inout, double rho, int n_steps, unsigned dirs_mask, void* stream);
+
 /* ---- auto-tuning ([W] Sec. 4.4 and Sec. 8) and device storage ------------- */
 
 /* Enables the auto-tuner: the first smearing call per (kernel, precision,

@@ -224,6 +224,12 @@ def stout_smear(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None, **opts):
                                    _stream(stream)), "lq_stout_smear")
 
 
+def stout_smear_noalloc(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
+    """lq_stout_smear_noalloc: same result as stout_smear, no device allocation (fields up to 32 MiB)."""
+    _check(L.load().lq_stout_smear_noalloc(links.handle, float(rho), int(n_steps), dirs_mask(dirs), _stream(stream)),
+           "lq_stout_smear_noalloc")
+
+
 def stout_smear_batch(fields, rho, n_steps, dirs=(0, 1, 2), stream=None, **opts):
     o = stout_opts(**opts)
     hs = (c_void_p * len(fields))(*[f.handle for f in fields])

@@ -53,6 +53,7 @@ SIGNATURES = {
     "lq_stout_smear": (c_int, [_P, c_double, c_int, c_uint, POINTER(LqStoutOpts), _P]),
     "lq_stout_backward": (c_int, [_P, c_double, c_int, c_uint, _P, c_double, _P, _P, POINTER(LqBackwardOpts), _P]),
     "lq_stout_smear_batch": (c_int, [POINTER(_P), c_int, c_double, c_int, c_uint, POINTER(LqStoutOpts), _P]),
+    "lq_stout_smear_noalloc": (c_int, [_P, c_double, c_int, c_uint, _P]),
     "lq_tune": (c_int, [ctypes.c_char_p]),
     "lq_tune_lookup": (c_int, [c_int, POINTER(c_int), c_uint, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "lq_free_all": (c_int, []),
