@@ -36,8 +36,42 @@ WORKLOAD = "48^3x96 periodic, exp(i*0.3*H) links seed 2, 6 stout steps rho=0.125
 METRIC = "stout link-updates/s"
 
 # Algorithmic counts per link update (4 smeared directions), derived in the design doc:
-# minimum traffic = read every link once + write every updated link once.
+# minimum traffic = read every link once + write every updated link once;
+# flops of the staple / Omega / Q / exp / U' matrix algebra, and of the FP64
+# Cayley-Hamilton coefficients (+ FP64 re-projection in the FP32 path).
 BYTES_PER_LINK = {"f32": 144.0, "f64": 288.0}
+MATRIX_FLOPS_PER_LINK = 3028.0
+CH_FLOPS_PER_LINK = 214.0
+REPROJECT_FLOPS_PER_LINK = 142.0
+# GB300 unit counts: 152 SMs x 2 FP64 FMA lanes (304 per cycle) and x 128 FP32 FMA lanes.
+FP64_FMA_PER_CLK = 304
+FP32_FMA_PER_CLK = 152 * 128
+# FP32 small-case (32^3x64) ncu DRAM bytes per launch of the FP32 step kernel divided by
+# its 8,388,608 link updates, times the 42,467,328 link updates of one 48^3x96 launch
+# (traffic grows in proportion to the links); see profiles/.
+TRAFFIC_BYTES_PER_LINK_F32 = (633602560 + 576611328) / 8388608.0
+TRAFFIC_BYTES_PER_LINK_F64 = (2051477760 + 1185383168) / 8388608.0
+
+
+def roofline(kernel_ms, links, prec, hbm_gbs, sm_mhz):
+    """Roofline of one step-kernel launch: time bound of each resource from the
+    algorithmic counts, the binding one reported as achieved / peak."""
+    f64_flops = CH_FLOPS_PER_LINK + (REPROJECT_FLOPS_PER_LINK if prec == "f32" else MATRIX_FLOPS_PER_LINK)
+    f32_flops = MATRIX_FLOPS_PER_LINK if prec == "f32" else 0.0
+    p64 = 2.0 * FP64_FMA_PER_CLK * sm_mhz * 1e6
+    p32 = 2.0 * FP32_FMA_PER_CLK * sm_mhz * 1e6
+    t = {"hbm": BYTES_PER_LINK[prec] * links / (hbm_gbs * 1e9), "fp64": f64_flops * links / p64,
+         "fp32": f32_flops * links / p32}
+    sec = kernel_ms * 1e-3
+    ach64 = f64_flops * links / sec / 1e12
+    traffic = (TRAFFIC_BYTES_PER_LINK_F32 if prec == "f32" else TRAFFIC_BYTES_PER_LINK_F64) * links
+    return {"bound": "alu", "pipe": "fp64", "achieved": ach64, "peak": p64 / 1e12, "unit": "TFLOP/s",
+            "frac": ach64 / (p64 / 1e12), "traffic": traffic,
+            "peak_source": f"derived: {FP64_FMA_PER_CLK} FP64 FMA/clk x 2 flops x {sm_mhz:.0f} MHz median SM clock",
+            "fp64_flops_per_link": f64_flops, "fp32_flops_per_link": f32_flops,
+            "bytes_per_link": BYTES_PER_LINK[prec], "kernel_ms": kernel_ms,
+            "t_bound_ms": {k: 1e3 * v for k, v in t.items()},
+            "hbm_frac": BYTES_PER_LINK[prec] * links / sec / 1e9 / hbm_gbs}
 
 
 def peaks():
@@ -107,6 +141,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, dist, device="cuda"):
+    """The largest `value` over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank processes units_per_rank in `seconds` (max over ranks)."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -160,7 +209,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--f64-steps", type=int, default=3)
     ap.add_argument("--dims", default=None, help="Lx,Ly,Lz,Lt override (smaller profiling cases)")
-    ap.add_argument("--workload", default="stout48", choices=["stout48", "batch64", "backward24", "micro16"],
+    ap.add_argument("--variant", type=int, default=0,
+                    help="step kernel: 0 auto-tuned (default), 1 global loads, 2 shared-memory staged (FP32)")
+    ap.add_argument("--workload", default="stout48", choices=["stout48", "batch64", "backward24", "micro16", "jacobi32"],
                     help="stout48 (default, the headline line); the others print their own JSON line")
     args = ap.parse_args()
     if args.workload != "stout48" and args.impl == "ours":
@@ -202,6 +253,9 @@ def main():
     f64 = lq.Field(g, lq.LQ_LINKS, lq.LQ_F64)
 
     stream = torch.cuda.current_stream()
+    if args.variant == 0:
+        lq.tune(None)   # launch shapes tuned on the first (warm-up) call, kept in memory
+    smear_opts = {"variant": args.variant} if args.variant else {}
 
     def barrier():
         torch.cuda.synchronize()
@@ -210,8 +264,9 @@ def main():
 
     def timed(field, steps, warmup):
         field.upload(U_host)
+        opts = smear_opts if field.prec == lq.LQ_F32 or args.variant != 2 else {}
         for _ in range(warmup):
-            lq.stout_smear(field, RHO, N_SMEAR, DIRS)
+            lq.stout_smear(field, RHO, N_SMEAR, DIRS, **opts)
             lq.plaquette(field)
         barrier()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -221,7 +276,7 @@ def main():
         t_all0.record(stream)
         for e0, e1, e2 in ev:
             e0.record(stream)
-            lq.stout_smear(field, RHO, N_SMEAR, DIRS)   # N_SMEAR launches of the fused step kernel
+            lq.stout_smear(field, RHO, N_SMEAR, DIRS, **opts)   # N_SMEAR launches of the fused step kernel
             e1.record(stream)
             lq.plaquette(field)                          # 2 launches, synchronises
             e2.record(stream)
@@ -229,11 +284,7 @@ def main():
         barrier()
         total_ms = t_all0.elapsed_time(t_all1)
         smear_ms = [a.elapsed_time(b) for a, b, _ in ev]
-        step_ms = total_ms / steps
-        if dist is not None:
-            t = torch.tensor([step_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            step_ms = float(t.item())
+        step_ms = max_over_ranks(total_ms / steps, dist)
         return step_ms, float(np.mean(smear_ms)) / N_SMEAR
 
     pk = peaks()
@@ -247,7 +298,7 @@ def main():
     # accuracy at the stated precision: fresh inputs, one 6-step smearing each
     f32.upload(U_host)
     f64.upload(U_host)
-    lq.stout_smear(f32, RHO, N_SMEAR, DIRS)
+    lq.stout_smear(f32, RHO, N_SMEAR, DIRS, **smear_opts)
     lq.stout_smear(f64, RHO, N_SMEAR, DIRS)
     p32, p64 = lq.plaquette(f32), lq.plaquette(f64)
     d32 = f32.download()
@@ -270,7 +321,7 @@ def main():
     e2e_steps = max(1, min(args.steps, 3))
     for _ in range(1):
         f32.upload_ptr(pin_in.data_ptr())
-        lq.stout_smear(f32, RHO, N_SMEAR, DIRS)
+        lq.stout_smear(f32, RHO, N_SMEAR, DIRS, **smear_opts)
         lq.plaquette(f32)
         f32.download_ptr(pin_out.data_ptr())
     barrier()
@@ -278,16 +329,12 @@ def main():
     e0.record(stream)
     for _ in range(e2e_steps):
         f32.upload_ptr(pin_in.data_ptr())
-        lq.stout_smear(f32, RHO, N_SMEAR, DIRS)
+        lq.stout_smear(f32, RHO, N_SMEAR, DIRS, **smear_opts)
         lq.plaquette(f32)
         f32.download_ptr(pin_out.data_ptr())
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -296,11 +343,20 @@ def main():
                "sample": f"1 FP64 stout step, 4 dirs, on 16^3x32 (same generator and rho): {n} link updates in {dt:.1f} s"}
 
     if rank == 0:
-        value = world * links_per_step / (step32 * 1e-3)
-        value64 = world * links_per_step / (step64 * 1e-3)
+        value = weak_scaling_value(links_per_step, world, step32 * 1e-3)
+        value64 = weak_scaling_value(links_per_step, world, step64 * 1e-3)
         links_per_launch = V * len(DIRS)
-        ach32 = BYTES_PER_LINK["f32"] * links_per_launch / (kern32 * 1e-3) / 1e9
-        ach64 = BYTES_PER_LINK["f64"] * links_per_launch / (kern64 * 1e-3) / 1e9
+        mhz = clocks.get("sm_mhz") or 2070.0
+        roof32 = roofline(kern32, links_per_launch, "f32", hbm, mhz)
+        tuned32 = lq.tune_lookup(lq.LQ_F32, DIMS, DIRS)
+        var32 = args.variant or (tuned32[2] if tuned32 else 1)
+        roof32["kernel"] = "k_stout_smem<float,reproject>" if var32 == 2 else "k_stout_global<float,reproject>"
+        roof32["launch"] = {"variant": var32, "tuned": tuned32}
+        if var32 == 2:
+            roof32["traffic"] = None   # DRAM counters of the shared-memory kernel not captured at this revision
+        roof64 = roofline(kern64, links_per_launch, "f64", hbm, mhz)
+        roof64["kernel"] = "k_stout_global<double>"
+        roof64["launch"] = {"variant": 1, "tuned": lq.tune_lookup(lq.LQ_F64, DIMS, DIRS)}
         out = {
             "metric": METRIC, "value": value, "unit": "link-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step32, "higher_is_better": True, "scaling": "weak",
@@ -308,16 +364,13 @@ def main():
             "precision": "FP32 matrix algebra and storage; FP64 Cayley-Hamilton coefficients, SU(3) re-projection and plaquette accumulation",
             "config": {"workload": WORKLOAD, "lattice": list(DIMS), "n_smear": N_SMEAR, "rho": RHO, "dirs": "xyzt",
                        "l2": "inputs larger than L2 (3.06 GB FP32 links)", "per_rank": "independent lattice per rank"},
-            "roofline": {"bound": "hbm", "achieved": ach32, "peak": hbm, "unit": "GB/s", "frac": ach32 / hbm,
-                         "traffic": None, "kernel": "k_stout_global<float,reproject>",
-                         "kernel_ms": kern32, "peak_source": "measured hbm_gbs"},
-            "fp64": {"value": value64, "ms_per_step": step64, "kernel_ms": kern64,
-                     "roofline": {"bound": "hbm", "achieved": ach64, "peak": hbm, "unit": "GB/s", "frac": ach64 / hbm}},
+            "roofline": roof32,
+            "fp64": {"value": value64, "ms_per_step": step64, "kernel_ms": kern64, "roofline": roof64},
             "fp32_speedup_vs_fp64": value / value64,
             "accuracy": {"fp32_vs_fp64_gpu_max_abs": err_32_64, "fp32_vs_oracle_sampled_max_abs": e32o,
                          "fp64_vs_oracle_sampled_max_abs": e64o, "plaquette_fp32": p32[0], "plaquette_fp64": p64[0],
                          "plaquette_abs_diff": abs(p32[0] - p64[0])},
-            "e2e": {"value": world * links_per_step / (e2e_ms * 1e-3), "unit": "link-updates/s",
+            "e2e": {"value": weak_scaling_value(links_per_step, world, e2e_ms * 1e-3), "unit": "link-updates/s",
                     "h2d_bytes_per_step": int(pin_in.numel() * 4), "d2h_bytes_per_step": int(pin_out.numel() * 4),
                     "ms_per_step": e2e_ms},
             "gpu_launches": args.steps * (N_SMEAR + 2),

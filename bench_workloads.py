@@ -8,6 +8,10 @@
 * backward24 -- 24^3 x 48, 3 stout steps rho = 0.1 in 4 dims, gradient of the
                 Wilson action (beta = 6) of the smeared field w.r.t. the thin
                 links, FP64 and FP32, every step checkpointed vs recomputed.
+* jacobi32   -- Jacobi smearing of Listing 1 (Sec. 6), the paper's own
+                application: 32^3 x 64 (the largest lattice of the paper's
+                Table 1), 20 iterations kappa = 0.21 over 4 directions, colour
+                vector and 4-spin fermion, FP32; and 24^3 x 48 in FP64.
 * micro16    -- 16^3 x 32, 10 spatial steps rho = 0.1 in FP64, and the fused
                 expression micro-suite on the same field: sum_mu tr(U_mu(x)
                 U_mu(x+mu)), U_mu(x) U_nu(x+mu)^dag, plaquette.
@@ -87,6 +91,45 @@ def backward24(args, torch, lq, fieldgen):
     return out
 
 
+# flops per site, spin and iteration: 8 colour matrix-vector products (66 each),
+# 7 vector sums (6 each), the axpy (12); bytes: 4 links + chi + s0 read, chi written
+JACOBI_FLOPS_PER_SPIN = 8 * 66 + 7 * 6 + 12
+
+
+def jacobi32(args, torch, lq, fieldgen):
+    import json as _json
+    import os
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out = {"metric": "Jacobi smearing GFLOP/s (Listing 1)", "unit": "GFLOP/s",
+           "config": {"workload": "Jacobi smearing, 20 iterations kappa=0.21, 4 dirs, exp(i*0.3*H) links",
+                      "paper_table1_context": "GTX 480: 21.31 GFLOPS SP at 32^3x64, 7.91 DP at 24^3x48 (whole routine)"}}
+    n_iter = 20
+    for name, dims, prec in (("f32_32c64", (32, 32, 32, 64), lq.LQ_F32), ("f64_24c48", (24, 24, 24, 48), lq.LQ_F64)):
+        V = int(np.prod(dims))
+        fU, _ = _field(lq, fieldgen, dims, 5, prec)
+        res = {}
+        for kind, nspin in (("vector", 1), ("fermion", 4)):
+            k = lq.LQ_COLOR_VECTOR if nspin == 1 else lq.LQ_FERMION
+            chi = lq.Field(fU.geom, k, prec)
+            chi.tensor.normal_()
+            t = _events(torch, lambda: lq.jacobi_smear(fU, chi, 0.21, n_iter, 1.0), args.steps, args.warmup)
+            eb = 8 if prec == lq.LQ_F32 else 16
+            bytes_site = 4 * 9 * eb + 3 * 3 * nspin * eb
+            flops = JACOBI_FLOPS_PER_SPIN * nspin * V * n_iter
+            res[kind] = {"ms": t, "gflops": flops / (t * 1e-3) / 1e9,
+                         "gb_s": bytes_site * V * n_iter / (t * 1e-3) / 1e9,
+                         "hbm_frac": bytes_site * V * n_iter / (t * 1e-3) / 1e9 / hbm}
+        out[name] = res
+    out["value"] = out["f32_32c64"]["vector"]["gflops"]
+    out["dtype"] = "f32"
+    return out
+
+
 def micro16(args, torch, lq, fieldgen):
     dims = (16, 16, 16, 32)
     V = int(np.prod(dims))
@@ -122,7 +165,7 @@ def run(args):
     import fieldgen
     import paper_1105_2279_gb300 as lq
     torch.cuda.set_device(0)
-    fn = {"batch64": batch64, "backward24": backward24, "micro16": micro16}[args.workload]
+    fn = {"batch64": batch64, "backward24": backward24, "micro16": micro16, "jacobi32": jacobi32}[args.workload]
     res = fn(args, torch, lq, fieldgen)
     res.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                 "data": "synthetic", "workload_mode": args.workload})

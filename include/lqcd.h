@@ -21,8 +21,9 @@
  *     complex number stored as (re, im) = float2 / double2, except kind
  *     LQ_REAL (one float / double).  A field of kind k holds
  *     [ndir][ncomp][V] elements with (ndir, ncomp) = LINKS (4, 9),
- *     COLOR_MATRIX (1, 9), COLOR_VECTOR (1, 3), COMPLEX (1, 1), REAL (1, 1);
- *     matrix component c = 3*row + col.  Consecutive threads read
+ *     COLOR_MATRIX (1, 9), COLOR_VECTOR (1, 3), COMPLEX (1, 1), REAL (1, 1),
+ *     FERMION (1, 12); matrix component c = 3*row + col, fermion component
+ *     c = 3*spin + colour.  Consecutive threads read
  *     consecutive sites of one component plane (coalesced 8/16 B vectors).
  *   - Host interchange layout (AoS, the QDP++ site-major order):
  *     [V][ndir][ncomp] elements of the field's precision, (re, im)
@@ -57,7 +58,7 @@ typedef int lq_status;
 #define LQ_ERR_UNSUPPORTED  (-7)  /* valid request this build does not implement        */
 
 typedef enum lq_kind {
-  LQ_LINKS = 0, LQ_COLOR_MATRIX = 1, LQ_COLOR_VECTOR = 2, LQ_COMPLEX = 3, LQ_REAL = 4
+  LQ_LINKS = 0, LQ_COLOR_MATRIX = 1, LQ_COLOR_VECTOR = 2, LQ_COMPLEX = 3, LQ_REAL = 4, LQ_FERMION = 5
 } lq_kind;
 
 typedef enum lq_prec { LQ_F32 = 0, LQ_F64 = 1 } lq_prec;
@@ -223,6 +224,23 @@ lq_status lq_stout_backward(const lq_field* thin_links, double rho, int n_steps,
  * Results equal n_cfg separate lq_stout_smear calls bit for bit. */
 lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, int n_steps,
                                unsigned dirs_mask, const lq_stout_opts* opts, void* stream);
+
+/* ---- Jacobi smearing ([W] Sec. 6, Listing 1 and the operator K) ----------- */
+
+/* n_iter Jacobi smearing iterations of a quark field, in place:
+ *   s0 = chi;  repeat n_iter times:
+ *     chi(x) <- s0(x) + kappa * sum_{mu in dirs} [U_mu(x) chi(x+mu) + U_mu(x-mu)^dag chi(x-mu)]
+ *   then chi /= norm
+ * (Listing 1; the hopping term is the off-diagonal part of the operator K).
+ * links: LINKS field; chi: COLOR_VECTOR (3 complex per site) or FERMION
+ * (4 spins x 3 colours; the links act on colour, every spin alike); same
+ * geometry and precision.  dirs_mask selects the summed directions (Listing 1
+ * sums all four; 7 leaves out t, like a smearing that skips the time
+ * direction).  norm != 0.  One fused kernel per iteration (hopping term, axpy
+ * and, in the last iteration, the 1/norm scaling) over two ping-pong buffers;
+ * scratch: s0 and one work copy of chi, allocated stream-ordered. */
+lq_status lq_jacobi_smear(const lq_field* links, lq_field* chi_inout, double kappa, int n_iter, double norm,
+                          unsigned dirs_mask, void* stream);
 
 /* Stout smearing that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot let a library

@@ -67,14 +67,18 @@ def trace_sum(field):
     return complex(np.sum(tr(field)))
 
 
-def jacobi_smear(U, chi, kappa, n_iter, norm):
+def jacobi_smear(U, chi, kappa, n_iter, norm, dirs=(0, 1, 2, 3)):
     """Listing 1 (Sec. 6): chi <- s0 + kappa * sum_mu [U_mu(x) psi(x+mu) + U_mu(x-mu)^dag psi(x-mu)],
-    iterated n_iter times from s0 = chi, then chi /= norm.  chi: (Lt,Lz,Ly,Lx,3)."""
+    iterated n_iter times from s0 = chi, then chi /= norm.  chi: (Lt,Lz,Ly,Lx,3), or
+    (Lt,Lz,Ly,Lx,4,3) for a fermion (the links act on colour, every spin alike)."""
+    if chi.ndim == 6:
+        return np.stack([jacobi_smear(U, chi[..., sp, :], kappa, n_iter, norm, dirs)
+                         for sp in range(chi.shape[-2])], axis=-2)
     s0 = chi.copy()
     for _ in range(n_iter):
         psi = chi.copy()
         h = np.zeros_like(psi)
-        for mu in range(ND):
+        for mu in dirs:
             Umu = U[..., mu, :, :]
             h += (Umu @ shift(psi, mu, +1)[..., None])[..., 0]
             h += shift((adj(Umu) @ psi[..., None])[..., 0], mu, -1)

@@ -14,13 +14,14 @@ from ctypes import byref, c_double, c_int, c_longlong, c_size_t, c_void_p
 import numpy as np
 
 from . import _lib as L
-from ._lib import (LQ_COLOR_MATRIX, LQ_COLOR_VECTOR, LQ_COMPLEX, LQ_F32, LQ_F64, LQ_LINKS,  # noqa: F401
-                   LQ_REAL, LqBackwardOpts, LqOp, LqStoutOpts)
+from ._lib import (LQ_COLOR_MATRIX, LQ_COLOR_VECTOR, LQ_COMPLEX, LQ_F32, LQ_F64, LQ_FERMION,  # noqa: F401
+                   LQ_LINKS, LQ_REAL, LqBackwardOpts, LqOp, LqStoutOpts)
 
 KIND_SHAPE = {LQ_LINKS: (4, 9), LQ_COLOR_MATRIX: (1, 9), LQ_COLOR_VECTOR: (1, 3), LQ_COMPLEX: (1, 1),
-              LQ_REAL: (1, 1)}
+              LQ_REAL: (1, 1), LQ_FERMION: (1, 12)}
 # per-site trailing shape of the host (AoS) arrays
-SITE_SHAPE = {LQ_LINKS: (4, 3, 3), LQ_COLOR_MATRIX: (3, 3), LQ_COLOR_VECTOR: (3,), LQ_COMPLEX: (), LQ_REAL: ()}
+SITE_SHAPE = {LQ_LINKS: (4, 3, 3), LQ_COLOR_MATRIX: (3, 3), LQ_COLOR_VECTOR: (3,), LQ_COMPLEX: (), LQ_REAL: (),
+              LQ_FERMION: (4, 3)}
 
 
 class LqError(RuntimeError):
@@ -228,6 +229,12 @@ def stout_smear_noalloc(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
     """lq_stout_smear_noalloc: same result as stout_smear, no device allocation (fields up to 32 MiB)."""
     _check(L.load().lq_stout_smear_noalloc(links.handle, float(rho), int(n_steps), dirs_mask(dirs), _stream(stream)),
            "lq_stout_smear_noalloc")
+
+
+def jacobi_smear(links, chi, kappa, n_iter, norm=1.0, dirs=(0, 1, 2, 3), stream=None):
+    """In-place Jacobi smearing of a COLOR_VECTOR or FERMION field (Listing 1)."""
+    _check(L.load().lq_jacobi_smear(links.handle, chi.handle, float(kappa), int(n_iter), float(norm),
+                                    dirs_mask(dirs), _stream(stream)), "lq_jacobi_smear")
 
 
 def stout_smear_batch(fields, rho, n_steps, dirs=(0, 1, 2), stream=None, **opts):

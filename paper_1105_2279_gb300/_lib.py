@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(PKG, "liblqcd.so")
 LQ_OK = 0
 STATUS_NAMES = {0: "LQ_OK", -1: "LQ_ERR_ARG", -2: "LQ_ERR_GEOM", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA",
                 -5: "LQ_ERR_TIMEOUT", -6: "LQ_ERR_NUMERIC", -7: "LQ_ERR_UNSUPPORTED"}
-LQ_LINKS, LQ_COLOR_MATRIX, LQ_COLOR_VECTOR, LQ_COMPLEX, LQ_REAL = range(5)
+LQ_LINKS, LQ_COLOR_MATRIX, LQ_COLOR_VECTOR, LQ_COMPLEX, LQ_REAL, LQ_FERMION = range(6)
 LQ_F32, LQ_F64 = 0, 1
 (LQ_OP_LOAD, LQ_OP_ADJ, LQ_OP_MUL, LQ_OP_ADD, LQ_OP_SUB, LQ_OP_SCALE, LQ_OP_TRACE, LQ_OP_RETR,
  LQ_OP_STORE) = range(9)
@@ -54,6 +54,7 @@ SIGNATURES = {
     "lq_stout_backward": (c_int, [_P, c_double, c_int, c_uint, _P, c_double, _P, _P, POINTER(LqBackwardOpts), _P]),
     "lq_stout_smear_batch": (c_int, [POINTER(_P), c_int, c_double, c_int, c_uint, POINTER(LqStoutOpts), _P]),
     "lq_stout_smear_noalloc": (c_int, [_P, c_double, c_int, c_uint, _P]),
+    "lq_jacobi_smear": (c_int, [_P, _P, c_double, c_int, c_double, c_uint, _P]),
     "lq_tune": (c_int, [ctypes.c_char_p]),
     "lq_tune_lookup": (c_int, [c_int, POINTER(c_int), c_uint, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "lq_free_all": (c_int, []),

@@ -2,6 +2,7 @@
 // device-storage release of liblqcd (device residency API of Winter,
 // "Accelerating QDP++ using GPUs", Sec. 5; coalesced layout, Sec. 8).
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -48,8 +49,20 @@ int device_sm_count() {
   return cached[d];
 }
 
+// Host-side fault injection for tests of the error paths: with the
+// environment variable LQ_FAULT_INJECT=alloc every library scratch allocation
+// fails with LQ_ERR_OOM before any CUDA call is made.
+static bool inject_alloc_failure() {
+  const char* v = getenv("LQ_FAULT_INJECT");
+  return v && strcmp(v, "alloc") == 0;
+}
+
 lq_status scratch_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
   *p = nullptr;
+  if (inject_alloc_failure()) {
+    set_error("%s: allocation of %zu bytes failed (fault injected by LQ_FAULT_INJECT=alloc)", what, bytes);
+    return LQ_ERR_OOM;
+  }
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
@@ -98,26 +111,52 @@ void register_cache_release(void (*fn)()) {
 }
 
 // ---- AoS <-> SoA transposes ------------------------------------------------
-// One thread per (site, element-in-site): reads of a warp are contiguous in
-// the AoS buffer, writes go to per-component planes.
+// A CTA moves a tile of kTileSites consecutive sites: the AoS side of the tile
+// is one contiguous run of kTileSites * per_site elements, each SoA plane gets
+// a contiguous run of kTileSites elements; the tile goes through shared memory
+// so that both global sides are accessed with consecutive addresses (the tile
+// rows are padded to per_site + 1 elements against shared-memory bank conflicts).
+constexpr int kTileSites = 64;
+constexpr int kTileThreads = 256;
+
 template <typename E>
-__global__ void aos_to_soa(const E* __restrict__ aos, E* __restrict__ soa, long long V, int per_site) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long n = V * per_site;
-  for (; i < n; i += (long long)gridDim.x * blockDim.x) {
-    long long s = i / per_site;
-    int c = (int)(i - s * per_site);
-    soa[(long long)c * V + s] = aos[i];
+__global__ void __launch_bounds__(kTileThreads) aos_to_soa(const E* __restrict__ aos, E* __restrict__ soa, long long V,
+                                                           int per_site) {
+  extern __shared__ __align__(16) unsigned char tile_raw[];
+  E* tile = reinterpret_cast<E*>(tile_raw);  // [kTileSites][per_site + 1]
+  const int ld = per_site + 1;
+  const long long s0 = (long long)blockIdx.x * kTileSites;
+  const int ns = (int)min((long long)kTileSites, V - s0);
+  const int n = ns * per_site;
+  const E* src = aos + s0 * per_site;
+  for (int i = threadIdx.x; i < n; i += kTileThreads) {
+    const int j = i / per_site, c = i - j * per_site;
+    tile[j * ld + c] = src[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += kTileThreads) {
+    const int c = i / ns, j = i - c * ns;
+    soa[(long long)c * V + s0 + j] = tile[j * ld + c];
   }
 }
 template <typename E>
-__global__ void soa_to_aos(const E* __restrict__ soa, E* __restrict__ aos, long long V, int per_site) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long n = V * per_site;
-  for (; i < n; i += (long long)gridDim.x * blockDim.x) {
-    long long s = i / per_site;
-    int c = (int)(i - s * per_site);
-    aos[i] = soa[(long long)c * V + s];
+__global__ void __launch_bounds__(kTileThreads) soa_to_aos(const E* __restrict__ soa, E* __restrict__ aos, long long V,
+                                                           int per_site) {
+  extern __shared__ __align__(16) unsigned char tile_raw[];
+  E* tile = reinterpret_cast<E*>(tile_raw);
+  const int ld = per_site + 1;
+  const long long s0 = (long long)blockIdx.x * kTileSites;
+  const int ns = (int)min((long long)kTileSites, V - s0);
+  const int n = ns * per_site;
+  for (int i = threadIdx.x; i < n; i += kTileThreads) {
+    const int c = i / ns, j = i - c * ns;
+    tile[j * ld + c] = soa[(long long)c * V + s0 + j];
+  }
+  __syncthreads();
+  E* dst = aos + s0 * per_site;
+  for (int i = threadIdx.x; i < n; i += kTileThreads) {
+    const int j = i / per_site, c = i - j * per_site;
+    dst[i] = tile[j * ld + c];
   }
 }
 
@@ -125,14 +164,13 @@ static lq_status transpose(const void* src, void* dst, const lq_field* f, bool t
   const long long V = f->geom.volume;
   const int per_site = ndir_of(f->kind) * ncomp_of(f->kind);
   const size_t eb = elem_bytes(f->kind, f->prec);
-  const long long n = V * per_site;
-  int blocks = (int)std::min<long long>((n + 255) / 256, (long long)device_sm_count() * 16);
-  if (blocks < 1) blocks = 1;
-#define LQ_T(E)                                                                                   \
-  if (to_soa)                                                                                     \
-    aos_to_soa<E><<<blocks, 256, 0, s>>>((const E*)src, (E*)dst, V, per_site);                   \
-  else                                                                                            \
-    soa_to_aos<E><<<blocks, 256, 0, s>>>((const E*)src, (E*)dst, V, per_site);
+  const unsigned blocks = (unsigned)((V + kTileSites - 1) / kTileSites);
+  const size_t smem = (size_t)kTileSites * (per_site + 1) * eb;  // <= 64 * 37 * 16 B = 37.9 KB
+#define LQ_T(E)                                                                                     \
+  if (to_soa)                                                                                       \
+    aos_to_soa<E><<<blocks, kTileThreads, smem, s>>>((const E*)src, (E*)dst, V, per_site);         \
+  else                                                                                              \
+    soa_to_aos<E><<<blocks, kTileThreads, smem, s>>>((const E*)src, (E*)dst, V, per_site);
   if (eb == 4) {
     LQ_T(float)
   } else if (eb == 8) {

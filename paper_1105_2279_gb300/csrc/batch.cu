@@ -211,6 +211,7 @@ extern "C" lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, dou
     for (int i = 1; i < n_cfg; ++i)
       if (links[i]->geom.volume > links[big]->geom.volume) big = i;
     if ((st = stout_choose(links[big], rho, dirs_mask, reproject, nullptr, s, &tc))) return st;
+    if (tc.variant != 1) tc = stout_default_choice(prec);  // the batch kernel reads through L1/L2
   }
   const bool use_graph = o && o->use_graph;
   register_cache_release(release_batch);

@@ -204,10 +204,15 @@ extern "C" lq_status lq_expr_eval(lq_field* out, const lq_op* prog, int n_ops, c
       set_error("lq_expr_eval: operand %d differs in geometry or precision", k);
       return LQ_ERR_GEOM;
     }
+    if (operands[k]->kind == LQ_FERMION) {
+      set_error("lq_expr_eval: FERMION operands are not supported by the 3x3 register machine");
+      return LQ_ERR_UNSUPPORTED;
+    }
   }
   if (out) {
-    if (!same_geom(out->geom, f0->geom) || out->prec != f0->prec || out->kind == LQ_LINKS) {
-      set_error("lq_expr_eval: output must share geometry/precision and not be LQ_LINKS");
+    if (!same_geom(out->geom, f0->geom) || out->prec != f0->prec || out->kind == LQ_LINKS ||
+        out->kind == LQ_FERMION) {
+      set_error("lq_expr_eval: output must share geometry/precision and not be LQ_LINKS or LQ_FERMION");
       return LQ_ERR_GEOM;
     }
     for (int k = 0; k < n_operands; ++k)

@@ -36,21 +36,25 @@ __device__ __forceinline__ float d2f(double d) {
   return __uint_as_float(f);
 }
 
-// 1/sqrt(a), a > 0 and a normal FP32 number: FP32 seed, two Newton steps
-// r <- r (3/2 - a r^2 / 2) (relative error 2^-22 -> 2^-44 -> rounding).
-__device__ __forceinline__ double rsqrt_nr(double a) {
+// NR = number of Newton steps after the FP32 seed (relative error ~2^-22):
+// 2 reaches FP64 rounding (used by the FP64 path), 1 gives ~1e-13, far below
+// the FP32 rounding of the FP32 path's matrix algebra.
+
+// 1/sqrt(a), a > 0 and a normal FP32 number: FP32 seed, Newton steps
+// r <- r (3/2 - a r^2 / 2).
+template <int NR = 2> __device__ __forceinline__ double rsqrt_nr(double a) {
   double r = f2d(rsqrtf(d2f(a)));
   const double ha = 0.5 * a;
-  r = r * fma(-ha * r, r, 1.5);
-  r = r * fma(-ha * r, r, 1.5);
+#pragma unroll
+  for (int i = 0; i < NR; ++i) r = r * fma(-ha * r, r, 1.5);
   return r;
 }
 
-// 1/a, a a normal FP32 number: FP32 seed, two Newton steps r <- r + r (1 - a r).
-__device__ __forceinline__ double rcp_nr(double a) {
+// 1/a, a a normal FP32 number: FP32 seed, Newton steps r <- r + r (1 - a r).
+template <int NR = 2> __device__ __forceinline__ double rcp_nr(double a) {
   double r = f2d(__frcp_rn(d2f(a)));
-  r = fma(r, fma(-a, r, 1.0), r);
-  r = fma(r, fma(-a, r, 1.0), r);
+#pragma unroll
+  for (int i = 0; i < NR; ++i) r = fma(r, fma(-a, r, 1.0), r);
   return r;
 }
 
@@ -58,10 +62,10 @@ __device__ __forceinline__ double rcp_nr(double a) {
 // Chebyshev cubic 4y^3 - 3y = x (cos 3t = 4cos^3 t - 3cos t), refined by two
 // Newton steps from an FP32 evaluation.  f'(y) = 12y^2 - 3 >= 6 on that range,
 // so an FP32 reciprocal of f' suffices for the step.
-__device__ __forceinline__ double cos_third_acos(double x) {
+template <int NR = 2> __device__ __forceinline__ double cos_third_acos(double x) {
   double y = f2d(cosf(acosf(d2f(x)) * (1.0f / 3.0f)));
 #pragma unroll
-  for (int it = 0; it < 2; ++it) {
+  for (int it = 0; it < NR; ++it) {
     const double y2 = y * y;
     const double f = fma(y, fma(4.0, y2, -3.0), -x);
     const double fp = fma(12.0, y2, -3.0);
@@ -128,6 +132,7 @@ __device__ __forceinline__ void sincos_red(double x, double* s, double* c) {
     sincos(x, s, c);
     return;
   }
+  // (a rho that produces |x| >= 2^20 has no physical use; the library covers it)
   const double k = rint(x * 0.63661977236758134);  // 2/pi
   double r = fma(-k, 1.5707963267948966, x);       // pi/2, leading double
   r = fma(-k, 6.123233995736766e-17, r);            // pi/2 - leading double

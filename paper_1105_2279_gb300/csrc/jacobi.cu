@@ -1,0 +1,165 @@
+// Jacobi smearing of a quark field (Winter, "Accelerating QDP++ using GPUs",
+// Sec. 6, Listing 1): the paper's application.  Listing 1 evaluates five
+// expressions per iteration (copy, the hopping term for the first and the
+// other directions, the axpy, the final scaling), one kernel each; here one
+// fused kernel per iteration forms
+//   chi'(x) = scale * (s0(x) + kappa * sum_mu [U_mu(x) chi(x+mu) + U_mu(x-mu)^dag chi(x-mu)])
+// with scale = 1/norm in the last iteration and 1 otherwise, for all spins of
+// a site at once (the links are read once per site).
+#include "lq_internal.h"
+#include "stout_core.cuh"
+
+namespace lq {
+
+template <typename R, int NSPIN>
+__global__ void __launch_bounds__(128) k_jacobi(const typename vec2<R>::type* __restrict__ U,
+                                                const typename vec2<R>::type* __restrict__ chi,
+                                                const typename vec2<R>::type* __restrict__ s0,
+                                                typename vec2<R>::type* __restrict__ out, GeomArgs g, R kappa,
+                                                R scale, unsigned dirs) {
+  typedef typename vec2<R>::type V2;
+  const long long V = g.V;
+  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const int s = (int)sl;
+  int c[4];
+  site_coords(g, s, c);
+  cx<R> h[NSPIN][3];
+#pragma unroll
+  for (int sp = 0; sp < NSPIN; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) h[sp][a] = mkc<R>(0, 0);
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    if (!((dirs >> mu) & 1u)) continue;
+    const int s_f = nb_fwd(g, s, c[mu], mu);
+    const int s_b = nb_bwd(g, s, c[mu], mu);
+    {
+      // U_mu(x) chi(x+mu)
+      const M3<R> u = ld_link<R>(U, V, mu, s);
+#pragma unroll
+      for (int sp = 0; sp < NSPIN; ++sp) {
+        cx<R> v[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const V2 e = __ldg(chi + (long long)(3 * sp + b) * V + s_f);
+          v[b] = mkc<R>(e.x, e.y);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) h[sp][a] = cfma(u.e[3 * a + b], v[b], h[sp][a]);
+      }
+    }
+    {
+      // U_mu(x-mu)^dag chi(x-mu)
+      const M3<R> u = ld_link<R>(U, V, mu, s_b);
+#pragma unroll
+      for (int sp = 0; sp < NSPIN; ++sp) {
+        cx<R> v[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const V2 e = __ldg(chi + (long long)(3 * sp + b) * V + s_b);
+          v[b] = mkc<R>(e.x, e.y);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) h[sp][a] = cfma_cn(u.e[3 * b + a], v[b], h[sp][a]);
+      }
+    }
+  }
+#pragma unroll
+  for (int sp = 0; sp < NSPIN; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long off = (long long)(3 * sp + a) * V + s;
+      const V2 e = __ldg(s0 + off);
+      V2 o;
+      o.x = scale * fmaR(kappa, h[sp][a].re, (R)e.x);
+      o.y = scale * fmaR(kappa, h[sp][a].im, (R)e.y);
+      out[off] = o;
+    }
+}
+
+template <typename R>
+__global__ void k_scale(typename vec2<R>::type* __restrict__ f, long long n, R scale) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    typename vec2<R>::type e = f[i];
+    e.x *= scale;
+    e.y *= scale;
+    f[i] = e;
+  }
+}
+
+template <typename R>
+static void launch_jacobi(int nspin, const void* U, const void* in, const void* s0, void* out, const GeomArgs& g,
+                          double kappa, double scale, unsigned dirs, cudaStream_t s) {
+  typedef typename vec2<R>::type V2;
+  const unsigned grid = (unsigned)((g.V + 127) / 128);
+  if (nspin == 4)
+    k_jacobi<R, 4><<<grid, 128, 0, s>>>((const V2*)U, (const V2*)in, (const V2*)s0, (V2*)out, g, (R)kappa, (R)scale,
+                                        dirs);
+  else
+    k_jacobi<R, 1><<<grid, 128, 0, s>>>((const V2*)U, (const V2*)in, (const V2*)s0, (V2*)out, g, (R)kappa, (R)scale,
+                                        dirs);
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+extern "C" lq_status lq_jacobi_smear(const lq_field* links, lq_field* chi, double kappa, int n_iter, double norm,
+                                     unsigned dirs_mask, void* stream) {
+  clear_error();
+  lq_status st = check_links(links, "lq_jacobi_smear");
+  if (st != LQ_OK) return st;
+  if ((st = check_dirs(dirs_mask, "lq_jacobi_smear")) != LQ_OK) return st;
+  if (!chi || (chi->kind != LQ_COLOR_VECTOR && chi->kind != LQ_FERMION)) {
+    set_error("lq_jacobi_smear: chi must be a COLOR_VECTOR or FERMION field");
+    return chi ? LQ_ERR_GEOM : LQ_ERR_ARG;
+  }
+  if (!same_geom(chi->geom, links->geom) || chi->prec != links->prec) {
+    set_error("lq_jacobi_smear: links and chi differ in geometry or precision");
+    return LQ_ERR_GEOM;
+  }
+  if (n_iter < 0 || !(norm == norm) || norm == 0.0 || !(kappa == kappa)) {
+    set_error("lq_jacobi_smear: n_iter >= 0, finite kappa and a finite non-zero norm are required");
+    return LQ_ERR_ARG;
+  }
+  cudaStream_t s = as_stream(stream);
+  const GeomArgs g = geom_args(chi->geom);
+  const int nspin = chi->kind == LQ_FERMION ? 4 : 1;
+  if (n_iter == 0) {
+    const long long n = g.V * 3 * nspin;
+    const int grid = (int)std::min<long long>((n + 255) / 256, (long long)device_sm_count() * 8);
+    if (chi->prec == LQ_F64)
+      k_scale<double><<<grid, 256, 0, s>>>((double2*)chi->ptr, n, 1.0 / norm);
+    else
+      k_scale<float><<<grid, 256, 0, s>>>((float2*)chi->ptr, n, (float)(1.0 / norm));
+    return launch_check("lq_jacobi_smear scale");
+  }
+  // chi stays s0 until the end; iterations ping-pong between two work buffers
+  void* w[2] = {nullptr, nullptr};
+  if ((st = scratch_alloc(&w[0], chi->bytes, s, "lq_jacobi_smear"))) return st;
+  if ((st = scratch_alloc(&w[1], chi->bytes, s, "lq_jacobi_smear"))) {
+    scratch_free(w[0], s);
+    return st;
+  }
+  const void* cur = chi->ptr;
+  for (int it = 0; it < n_iter && st == LQ_OK; ++it) {
+    void* out = w[it & 1];
+    const double scale = (it == n_iter - 1) ? 1.0 / norm : 1.0;
+    if (chi->prec == LQ_F64)
+      launch_jacobi<double>(nspin, links->ptr, cur, chi->ptr, out, g, kappa, scale, dirs_mask, s);
+    else
+      launch_jacobi<float>(nspin, links->ptr, cur, chi->ptr, out, g, kappa, scale, dirs_mask, s);
+    st = launch_check("lq_jacobi_smear kernel");
+    cur = out;
+  }
+  if (st == LQ_OK)
+    st = cuda_check(cudaMemcpyAsync(chi->ptr, cur, chi->bytes, cudaMemcpyDeviceToDevice, s), "lq_jacobi_smear copy");
+  scratch_free(w[0], s);
+  scratch_free(w[1], s);
+  return st;
+}

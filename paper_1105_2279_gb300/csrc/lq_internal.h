@@ -35,6 +35,7 @@ inline int ncomp_of(int kind) {
     case LQ_LINKS:
     case LQ_COLOR_MATRIX: return 9;
     case LQ_COLOR_VECTOR: return 3;
+    case LQ_FERMION: return 12;
     default: return 1;
   }
 }
@@ -42,7 +43,7 @@ inline size_t elem_bytes(int kind, int prec) {
   size_t r = prec == LQ_F64 ? 8 : 4;
   return kind == LQ_REAL ? r : 2 * r;
 }
-inline bool valid_kind(int k) { return k >= LQ_LINKS && k <= LQ_REAL; }
+inline bool valid_kind(int k) { return k >= LQ_LINKS && k <= LQ_FERMION; }
 inline bool valid_prec(int p) { return p == LQ_F32 || p == LQ_F64; }
 inline size_t field_bytes(const lq_geom& g, int kind, int prec) {
   return (size_t)g.volume * ndir_of(kind) * ncomp_of(kind) * elem_bytes(kind, prec);

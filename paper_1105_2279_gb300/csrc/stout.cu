@@ -41,6 +41,112 @@ __global__ void __launch_bounds__(256) k_stout_global(const typename vec2<R>::ty
   }
 }
 
+// Variant 2 (FP32): shared-memory staging.  A CTA owns a BX x BY x BZ block of
+// (x, y, z) and marches along t over `tchunk` slices, keeping a ring of three
+// t-slices (t-1, t, t+1) of all four link directions on the block plus a
+// one-site halo in shared memory; every staple link then comes from shared
+// memory.  The arithmetic and its order equal variant 1, so results are
+// bit-identical.
+constexpr int kSmemBX = 4, kSmemBY = 4, kSmemBZ = 4;
+constexpr int kSmemThreads = kSmemBX * kSmemBY * kSmemBZ * 4;
+constexpr int kSmemHS = (kSmemBX + 2) * (kSmemBY + 2) * (kSmemBZ + 2);
+
+template <typename R>
+__device__ __forceinline__ M3<R> sm_link(const typename vec2<R>::type* __restrict__ slot_base, int dir, int h) {
+  M3<R> m;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const typename vec2<R>::type v = slot_base[(dir * 9 + c) * kSmemHS + h];
+    m.e[c].re = v.x;
+    m.e[c].im = v.y;
+  }
+  return m;
+}
+
+template <typename R, bool REPRO>
+__global__ void __launch_bounds__(kSmemThreads, 1) k_stout_smem(const typename vec2<R>::type* __restrict__ Uin,
+                                                                 typename vec2<R>::type* __restrict__ Uout,
+                                                                 GeomArgs g, R rho, unsigned dirs, int nd,
+                                                                 MuList ml, int tchunk) {
+  typedef typename vec2<R>::type V2;
+  constexpr int BX = kSmemBX, BY = kSmemBY, BZ = kSmemBZ, HX = BX + 2, HY = BY + 2, HS = kSmemHS;
+  constexpr int NB = BX * BY * BZ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V2* sm = reinterpret_cast<V2*>(smem_raw);  // [3 slots][36 planes][HS]
+  const int ntx = (g.L[0] + BX - 1) / BX, nty = (g.L[1] + BY - 1) / BY, ntz = (g.L[2] + BZ - 1) / BZ;
+  int b = blockIdx.x;
+  const int x0 = (b % ntx) * BX;
+  b /= ntx;
+  const int y0 = (b % nty) * BY;
+  b /= nty;
+  const int z0 = (b % ntz) * BZ;
+  b /= ntz;
+  const int t0 = b * tchunk;
+  const int t1 = min(t0 + tchunk, g.L[3]);
+  const int tid = threadIdx.x;
+  const int mi = tid / NB, ls = tid % NB;
+  const int lx = ls % BX, ly = (ls / BX) % BY, lz = ls / (BX * BY);
+  const long long V = g.V;
+  const int mu = mi == 0 ? ml.mu[0] : (mi == 1 ? ml.mu[1] : (mi == 2 ? ml.mu[2] : ml.mu[3]));
+  const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+  const bool active = mi < nd && x < g.L[0] && y < g.L[1] && z < g.L[2];
+  // halo index of this thread's site and the unit steps along x, y, z
+  const int hc = (lx + 1) + HX * ((ly + 1) + HY * (lz + 1));
+
+  auto load_slice = [&](int t) {  // t in [-1, Lt]; periodic
+    const int tw = (t + g.L[3]) % g.L[3];
+    V2* dst = sm + (size_t)((t + 3) % 3) * 36 * HS;
+    for (int i = tid; i < 36 * HS; i += kSmemThreads) {
+      const int p = i / HS, h = i - p * HS;
+      const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+      const int gx = (x0 - 1 + hx + g.L[0]) % g.L[0];
+      const int gy = (y0 - 1 + hy + g.L[1]) % g.L[1];
+      const int gz = (z0 - 1 + hz + g.L[2]) % g.L[2];
+      dst[i] = __ldg(Uin + (long long)p * V + (gx + g.L[0] * (gy + g.L[1] * (gz + g.L[2] * tw))));
+    }
+  };
+  // link `dir` at the site displaced by (+-1 along a, +-1 along b) from this thread's site
+  auto link = [&](int t, int dir, int a, int da, int bdir, int db) -> M3<R> {
+    int h = hc, dt = 0;
+    if (a == 3) dt += da; else h += da * (a == 0 ? 1 : (a == 1 ? HX : HX * HY));
+    if (bdir == 3) dt += db; else h += db * (bdir == 0 ? 1 : (bdir == 1 ? HX : HX * HY));
+    return sm_link<R>(sm + (size_t)((t + dt + 3) % 3) * 36 * HS, dir, h);
+  };
+
+  for (int t = t0; t < t1; ++t) {
+    if (t == t0) {
+      load_slice(t - 1);
+      load_slice(t);
+    }
+    load_slice(t + 1);
+    __syncthreads();
+    if (active) {
+      M3<R> S;
+      m_zero(S);
+#pragma unroll
+      for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu || !((dirs >> nu) & 1u)) continue;
+        {
+          // U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+          M3<R> tmp = mul_nd(link(t, mu, nu, 1, nu, 0), link(t, nu, mu, 1, mu, 0));
+          mac_nn(S, link(t, nu, nu, 0, nu, 0), tmp);
+        }
+        {
+          // U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+          M3<R> tmp = mul_nn(link(t, mu, nu, -1, nu, 0), link(t, nu, nu, -1, mu, 1));
+          mac_dn(S, link(t, nu, nu, -1, nu, 0), tmp);
+        }
+      }
+      const M3<R> Up = stout_update<R>(S, link(t, mu, mu, 0, mu, 0), rho, REPRO);
+      const int s = x + g.L[0] * (y + g.L[1] * (z + g.L[2] * t));
+      st_m3<R>(Uout + (long long)mu * 9 * V + s, V, Up);
+    }
+    __syncthreads();
+  }
+}
+
+static size_t smem_bytes_f32() { return (size_t)3 * 36 * kSmemHS * sizeof(float2); }
+
 static MuList mu_list(unsigned dirs, int* n) {
   MuList m;
   int k = 0;
@@ -56,6 +162,29 @@ static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int
   const GeomArgs g = geom_args(geom);
   int nd = 0;
   const MuList ml = mu_list(dirs, &nd);
+  if (tc.variant == 2 && prec == LQ_F32) {
+    static bool attr_set[64] = {false};
+    const int dev = current_device();
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+      lq_status st = cuda_check(cudaFuncSetAttribute(k_stout_smem<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem_bytes_f32()), "stout smem attribute");
+      if (st == LQ_OK)
+        st = cuda_check(cudaFuncSetAttribute(k_stout_smem<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes_f32()), "stout smem attribute");
+      if (st != LQ_OK) return st;
+      attr_set[dev] = true;
+    }
+    const int tchunk = tc.nsite > 0 ? tc.nsite : 8;
+    const long long ntiles = (long long)((g.L[0] + kSmemBX - 1) / kSmemBX) * ((g.L[1] + kSmemBY - 1) / kSmemBY) *
+                             ((g.L[2] + kSmemBZ - 1) / kSmemBZ) * ((g.L[3] + tchunk - 1) / tchunk);
+    if (reproject)
+      k_stout_smem<float, true><<<(unsigned)ntiles, kSmemThreads, smem_bytes_f32(), s>>>(
+          (const float2*)in, (float2*)out, g, (float)rho, dirs, nd, ml, tchunk);
+    else
+      k_stout_smem<float, false><<<(unsigned)ntiles, kSmemThreads, smem_bytes_f32(), s>>>(
+          (const float2*)in, (float2*)out, g, (float)rho, dirs, nd, ml, tchunk);
+    return launch_check("stout step kernel (shared-memory variant)");
+  }
   const int block = tc.block > 0 ? tc.block : 128;
   const int nsite = tc.nsite > 0 ? tc.nsite : 1;
   const long long per_block = (long long)block * nsite;
@@ -150,6 +279,28 @@ static lq_status stout_autotune(const lq_field* f, double rho, unsigned dirs, in
         *best = c;
       }
     }
+  if (st == LQ_OK && f->prec == LQ_F32) {
+    const int tchunks[] = {4, 8, 16};
+    for (int tcn : tchunks) {
+      TuneChoice c;
+      c.block = kSmemThreads;
+      c.nsite = tcn;
+      c.variant = 2;
+      st = launch_step(f->ptr, tmp, f->geom, f->prec, rho, dirs, reproject, c, s);
+      if (st != LQ_OK) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 2; ++r) launch_step(f->ptr, tmp, f->geom, f->prec, rho, dirs, reproject, c, s);
+      cudaEventRecord(e1, s);
+      st = cuda_check(cudaEventSynchronize(e1), "stout autotune timing");
+      if (st != LQ_OK) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        *best = c;
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   scratch_free(tmp, s);
@@ -158,10 +309,15 @@ static lq_status stout_autotune(const lq_field* f, double rho, unsigned dirs, in
 
 lq_status stout_choose(const lq_field* f, double rho, unsigned dirs, int reproject, const lq_stout_opts* o,
                        cudaStream_t s, TuneChoice* out) {
-  if (o && o->block > 0) {
-    out->block = o->block;
-    out->nsite = o->sites_per_thread > 0 ? o->sites_per_thread : 1;
+  if (o && (o->block > 0 || o->variant > 0)) {  // explicit launch shape
     out->variant = o->variant > 0 ? o->variant : 1;
+    if (out->variant == 2) {
+      out->block = kSmemThreads;
+      out->nsite = o->sites_per_thread > 0 ? o->sites_per_thread : 8;  // t-slices per CTA
+    } else {
+      out->block = o->block > 0 ? o->block : 128;
+      out->nsite = o->sites_per_thread > 0 ? o->sites_per_thread : 1;
+    }
     return LQ_OK;
   }
   *out = stout_default_choice(f->prec);
@@ -273,11 +429,15 @@ extern "C" lq_status lq_stout_smear(lq_field* links, double rho, int n_steps, un
     set_error("lq_stout_smear: opts->struct_size %d < sizeof(lq_stout_opts)", opts->struct_size);
     return LQ_ERR_ARG;
   }
-  if (o && o->variant > 1) {
-    set_error("lq_stout_smear: variant %d is not available", o->variant);
+  if (o && (o->variant < 0 || o->variant > 2)) {
+    set_error("lq_stout_smear: variant %d is not available (0 tuned, 1 global, 2 shared memory)", o->variant);
     return LQ_ERR_UNSUPPORTED;
   }
-  if (o && o->block > 0 && (o->block % 32 != 0 || o->block > 256)) {
+  if (o && o->variant == 2 && links->prec != LQ_F32) {
+    set_error("lq_stout_smear: the shared-memory variant is built for FP32 links only");
+    return LQ_ERR_UNSUPPORTED;
+  }
+  if (o && o->block > 0 && o->variant != 2 && (o->block % 32 != 0 || o->block > 256)) {
     set_error("lq_stout_smear: block %d must be a multiple of 32 in [32, 256]", o->block);
     return LQ_ERR_ARG;
   }

@@ -121,6 +121,7 @@ struct CHCoef {
 //   1/sqrt(c1/3) by Newton;  |c0|/c0max = |c0| (1/sqrt(c1/3))^3 / 2;
 //   cos(theta/3) as the root of 4y^3 - 3y = |c0|/c0max;  w^2 = c1 (1 - y^2);
 //   cos w and xi0(w) = sin(w)/w from w^2 by their series when w <= pi/4.
+template <int NR = 2>
 __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d2, cx<double> o01,
                                                   cx<double> o02, cx<double> o12) {
   CHCoef f;
@@ -142,10 +143,10 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
   }
   const bool neg = c0 < 0.0;
   const double a = c1 * (1.0 / 3.0);
-  const double r3 = rsqrt_nr(a);                                   // 1/sqrt(c1/3)
+  const double r3 = rsqrt_nr<NR>(a);                               // 1/sqrt(c1/3)
   const double s3 = a * r3;                                        // sqrt(c1/3)
   const double x = fmin(0.5 * fabs(c0) * (r3 * r3 * r3), 1.0);     // |c0| / c0max
-  const double y = cos_third_acos(x);                              // cos(theta/3)
+  const double y = cos_third_acos<NR>(x);                          // cos(theta/3)
   const double u = s3 * y;
   const double u2 = u * u;
   const double w2 = fmax(c1 * ((1.0 - y) * (1.0 + y)), 0.0);       // w^2 = c1 sin^2(theta/3)
@@ -153,7 +154,7 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
   if (w2 <= 0.61685027506808491) {                                 // w <= pi/4
     cos_sinc_from_sq(w2, &cw, &xi0);
   } else {
-    const double rw = rsqrt_nr(w2);
+    const double rw = rsqrt_nr<NR>(w2);
     double sw;
     sincos_red(w2 * rw, &sw, &cw);
     xi0 = sw * rw;
@@ -169,7 +170,7 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
   const cx<double> h1 = csub(cscale(e2iu, 2.0 * u), cmul(emiu, mkc(2.0 * u * cw, -(3.0 * u2 - w2) * xi0)));
   // h2 = e^{2iu} - e^{-iu} [cos w + 3iu xi0]
   const cx<double> h2 = csub(e2iu, cmul(emiu, mkc(cw, 3.0 * u * xi0)));
-  const double inv = rcp_nr(9.0 * u2 - w2);   // 9u^2 - w^2 >= 2 c1 > 0
+  const double inv = rcp_nr<NR>(9.0 * u2 - w2);   // 9u^2 - w^2 >= 2 c1 > 0
   f.f0 = cscale(h0, inv);
   f.f1 = cscale(h1, inv);
   f.f2 = cscale(h2, inv);
@@ -302,29 +303,40 @@ __device__ __forceinline__ M3<R> expiq_assemble(const QH<R>& q, const QH<R>& q2,
 }
 
 // SU(3) re-projection in FP64: Gram-Schmidt of rows 0 and 1, row 2 = conj(row0 x row1).
-__device__ __forceinline__ void reproject_f64(M3<double>& m) {
-  double n0 = 0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) n0 += cnorm2(m.e[k]);
-  const double r0 = rsqrt_nr(n0);
+// Written as FMA chains (norms, row1 - p row0, the cross product) to keep
+// the FP64 instruction count low.
+__device__ __forceinline__ double row_norm2(const cx<double>* r) {
+  double n = r[0].re * r[0].re;
+  n = fma(r[0].im, r[0].im, n);
+  n = fma(r[1].re, r[1].re, n);
+  n = fma(r[1].im, r[1].im, n);
+  n = fma(r[2].re, r[2].re, n);
+  return fma(r[2].im, r[2].im, n);
+}
+template <int NR = 2> __device__ __forceinline__ void reproject_f64(M3<double>& m) {
+  const double r0 = rsqrt_nr<NR>(row_norm2(&m.e[0]));
 #pragma unroll
   for (int k = 0; k < 3; ++k) m.e[k] = cscale(m.e[k], r0);
-  cx<double> p = mkc(0.0, 0.0);
+  // p = sum_k conj(row0_k) row1_k;  row1 <- row1 - p row0
+  cx<double> p = mkc(m.e[0].re * m.e[3].re, m.e[0].re * m.e[3].im);
+  p.re = fma(m.e[0].im, m.e[3].im, p.re);
+  p.im = fma(-m.e[0].im, m.e[3].re, p.im);
+  p = cfma_cn(m.e[1], m.e[4], p);
+  p = cfma_cn(m.e[2], m.e[5], p);
+  const cx<double> mp = mkc(-p.re, -p.im);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) p = cfma_cn(m.e[k], m.e[3 + k], p);  // sum conj(r0_k) row1_k
-  double n1 = 0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    m.e[3 + k] = csub(m.e[3 + k], cmul(p, m.e[k]));
-    n1 += cnorm2(m.e[3 + k]);
-  }
-  const double r1 = rsqrt_nr(n1);
+  for (int k = 0; k < 3; ++k) m.e[3 + k] = cfma(mp, m.e[k], m.e[3 + k]);
+  const double r1 = rsqrt_nr<NR>(row_norm2(&m.e[3]));
 #pragma unroll
   for (int k = 0; k < 3; ++k) m.e[3 + k] = cscale(m.e[3 + k], r1);
-  // row2 = conj(row0 x row1)
-  m.e[6] = cconj(csub(cmul(m.e[1], m.e[5]), cmul(m.e[2], m.e[4])));
-  m.e[7] = cconj(csub(cmul(m.e[2], m.e[3]), cmul(m.e[0], m.e[5])));
-  m.e[8] = cconj(csub(cmul(m.e[0], m.e[4]), cmul(m.e[1], m.e[3])));
+  // row2 = conj(row0 x row1), each entry a*b - c*d as one product and one complex FMA
+  auto cross = [&](int a, int b, int c, int d) {
+    const cx<double> t = cmul(m.e[c], m.e[d]);
+    return cconj(cfma(m.e[a], m.e[b], mkc(-t.re, -t.im)));
+  };
+  m.e[6] = cross(1, 5, 2, 4);
+  m.e[7] = cross(2, 3, 0, 5);
+  m.e[8] = cross(0, 4, 1, 3);
 }
 
 template <typename A, typename B> __device__ __forceinline__ M3<A> m_convert(const M3<B>& m) {
@@ -347,24 +359,22 @@ template <typename R> __device__ __forceinline__ M3<R> reproject_via_f64(const M
   M3<double> d;
 #pragma unroll
   for (int i = 0; i < 6; ++i) d.e[i] = mkc(to_f64(m.e[i].re), to_f64(m.e[i].im));
-  reproject_f64(d);
+  reproject_f64<sizeof(R) == 4 ? 1 : 2>(d);
   M3<R> r;
 #pragma unroll
   for (int i = 0; i < 9; ++i) r.e[i] = mkc<R>(from_f64<R>(d.e[i].re), from_f64<R>(d.e[i].im));
   return r;
 }
 
-// New link U'_mu(x) for one (site, mu): FP64 coefficients always; matrix
-// algebra in R; optional FP64 re-projection.
+// New link from the bare staple sum S and U_mu(x): FP64 coefficients always;
+// matrix algebra in R; optional FP64 re-projection.
 template <typename R>
-__device__ __forceinline__ M3<R> stout_link(const typename vec2<R>::type* __restrict__ U,
-                                            const GeomArgs& g, int s, const int c[4], int mu,
-                                            unsigned dirs, R rho, bool reproject) {
-  const M3<R> C = m_rscale(staple_sum<R>(U, g, s, c, mu, dirs), rho);
-  const M3<R> Umu = ld_link<R>(U, g.V, mu, s);
+__device__ __forceinline__ M3<R> stout_update(const M3<R>& S, const M3<R>& Umu, R rho, bool reproject) {
+  const M3<R> C = m_rscale(S, rho);
   const M3<R> Om = mul_nd(C, Umu);
   const QH<R> q = q_from_omega(Om);
-  const CHCoef f = ch_coefficients(to_f64(q.d0), to_f64(q.d1), to_f64(q.d2),
+  // FP32 links: one Newton step per FP64 refinement (~1e-13); FP64 links: two
+  const CHCoef f = ch_coefficients<sizeof(R) == 4 ? 1 : 2>(to_f64(q.d0), to_f64(q.d1), to_f64(q.d2),
                                    mkc(to_f64(q.o01.re), to_f64(q.o01.im)), mkc(to_f64(q.o02.re), to_f64(q.o02.im)),
                                    mkc(to_f64(q.o12.re), to_f64(q.o12.im)));
   const QH<R> q2 = q_square(q);
@@ -374,6 +384,14 @@ __device__ __forceinline__ M3<R> stout_link(const typename vec2<R>::type* __rest
   M3<R> Up = mul_nn(E, Umu);
   if (reproject) Up = reproject_via_f64(Up);
   return Up;
+}
+
+// New link U'_mu(x) for one (site, mu), neighbours read from global memory.
+template <typename R>
+__device__ __forceinline__ M3<R> stout_link(const typename vec2<R>::type* __restrict__ U,
+                                            const GeomArgs& g, int s, const int c[4], int mu,
+                                            unsigned dirs, R rho, bool reproject) {
+  return stout_update<R>(staple_sum<R>(U, g, s, c, mu, dirs), ld_link<R>(U, g.V, mu, s), rho, reproject);
 }
 
 }  // namespace lq

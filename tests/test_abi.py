@@ -100,3 +100,22 @@ def test_expr_program_validation(lqlib):
         arr, n = lqlib.compile_program(prog)
         assert lib.lq_expr_eval(None, arr, n, ops, 1, red, None) == -1
     lib.lq_field_free(h)
+
+
+def test_injected_allocation_failure_is_reported(lqlib, monkeypatch):
+    """LQ_FAULT_INJECT=alloc makes the library's scratch allocations fail on the
+    host: calls return LQ_ERR_OOM with a message and launch nothing (the fake
+    device pointer below is never dereferenced)."""
+    lib = lqlib.capi()
+    g = lqlib.Geometry((4, 4, 4, 4))
+    h = ctypes.c_void_p()
+    need = lqlib.field_bytes(g, lqlib.LQ_LINKS, lqlib.LQ_F64)
+    assert lib.lq_field_wrap(g.handle, 0, 1, ctypes.c_void_p(0x1000), need, ctypes.byref(h)) == 0
+    monkeypatch.setenv("LQ_FAULT_INJECT", "alloc")
+    assert lib.lq_stout_smear(h, 0.1, 2, 15, None, None) == -3
+    assert b"fault injected" in lib.lq_last_error()
+    out = (ctypes.c_double * 3)()
+    assert lib.lq_plaquette(h, out, None) == -3
+    assert lib.lq_stout_backward(h, 0.1, 1, 15, None, 6.0, h, None, None, None) in (-1, -3)
+    monkeypatch.delenv("LQ_FAULT_INJECT")
+    lib.lq_field_free(h)

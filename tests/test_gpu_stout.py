@@ -108,6 +108,28 @@ def test_launch_shapes_graph_and_workspace_agree_bitwise(gpu, prec):
     assert np.array_equal(f.download(), base)
 
 
+@pytest.mark.parametrize("dims,dirs", [((8, 8, 8, 16), ALL), ((5, 6, 7, 9), ALL), ((3, 4, 5, 6), SPATIAL),
+                                       ((2, 2, 2, 2), ALL), ((1, 4, 3, 5), (1, 2, 3)), ((12, 4, 8, 3), (0, 3))])
+def test_shared_memory_variant_bitwise_equal(gpu, dims, dirs):
+    """The shared-memory staged kernel (FP32) performs the same arithmetic in the
+    same order as the global-load kernel: results are bit-identical, for ragged
+    tiles, lattices smaller than a tile and any number of t-slices per block."""
+    U = fieldgen.near_identity_su3(dims, 108)
+    base = _run(U, lq.LQ_F32, 0.1, 3, dirs, block=128, sites_per_thread=1)
+    for tchunk in (1, 3, 8, 100):
+        got = _run(U, lq.LQ_F32, 0.1, 3, dirs, variant=2, sites_per_thread=tchunk)
+        assert np.array_equal(got, base), tchunk
+    got = _run(U, lq.LQ_F32, 0.1, 2, dirs, variant=2, reproject=False)
+    assert np.array_equal(got, _run(U, lq.LQ_F32, 0.1, 2, dirs, block=64, reproject=False))
+
+
+def test_shared_memory_variant_is_fp32_only(gpu):
+    f = upload_links(fieldgen.unit_links((2, 2, 2, 2)), lq.LQ_F64)
+    with pytest.raises(lq.LqError) as e:
+        lq.stout_smear(f, 0.1, 1, ALL, variant=2)
+    assert e.value.status == -7
+
+
 def test_autotuner_keeps_results(gpu, tmp_path):
     dims = (6, 4, 4, 8)
     U = fieldgen.near_identity_su3(dims, 107)

@@ -74,3 +74,30 @@ def test_jacobi_gauge_covariant():
     a = expr.jacobi_smear(gauge.gauge_transform(U, g), (g @ chi[..., None])[..., 0], 0.2, 3, 1.0)
     b = (g @ expr.jacobi_smear(U, chi, 0.2, 3, 1.0)[..., None])[..., 0]
     assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_jacobi_subset_of_directions_and_fermion():
+    """With unit links a plane wave is an eigenvector of the hopping term summed
+    over `dirs` with eigenvalue 2 sum_{mu in dirs} cos p_mu; a fermion is smeared
+    spin by spin (the links act on colour only)."""
+    dims = (4, 4, 4, 8)
+    U = fieldgen.unit_links(dims)
+    n = np.array([1, 3, 2, 5])
+    p = 2 * np.pi * n / np.array(dims)
+    lt, lz, ly, lx = lattice.field_shape(dims)
+    t, z, y, x = np.meshgrid(range(lt), range(lz), range(ly), range(lx), indexing="ij")
+    phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    spins = np.array([[0.3, -1.0, 0.5j], [1j, 0.2, 0.0], [0.0, 0.0, 1.0], [-0.5, 0.25j, 2.0]])
+    chi = phase[..., None, None] * spins
+    kappa, n_iter, norm, dirs = 0.17, 4, 2.0, (0, 1, 2)
+    lam = 2 * np.sum(np.cos(p[list(dirs)]))
+    coef = sum((kappa * lam) ** k for k in range(n_iter + 1)) / norm
+    got = expr.jacobi_smear(U, chi, kappa, n_iter, norm, dirs)
+    assert np.max(np.abs(got - coef * chi)) < 1e-12
+    Uh = fieldgen.haar_su3(dims, 46)
+    f = fieldgen.color_vector(dims, 47)
+    ferm = np.stack([f, 2 * f, -f, 1j * f], axis=-2)
+    one = expr.jacobi_smear(Uh, f, kappa, 2, norm, dirs)
+    both = expr.jacobi_smear(Uh, ferm, kappa, 2, norm, dirs)
+    for sp, c in enumerate((1, 2, -1, 1j)):
+        assert np.max(np.abs(both[..., sp, :] - c * one)) < 1e-12
