@@ -57,6 +57,48 @@ static bool inject_alloc_failure() {
   return v && strcmp(v, "alloc") == 0;
 }
 
+// The library's own stream-ordered memory pool per device.  Unlike the
+// device's default pool (release threshold 0: memory goes back to the driver
+// at every synchronisation) it keeps freed memory for the next call, so
+// repeated smearing / transfer calls do not re-map gigabytes each time;
+// lq_free_all trims it.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {nullptr};
+
+static lq_status library_pool(cudaMemPool_t* out) {
+  const int dev = current_device();
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range", dev);
+    return LQ_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    lq_status st = cuda_check(cudaMemPoolCreate(&pool, &props), "memory pool");
+    if (st != LQ_OK) return st;
+    unsigned long long keep = ~0ull;
+    st = cuda_check(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep), "memory pool threshold");
+    if (st != LQ_OK) {
+      cudaMemPoolDestroy(pool);
+      return st;
+    }
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return LQ_OK;
+}
+
+static void trim_pools() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (int d = 0; d < 64; ++d)
+    if (g_pool[d]) cudaMemPoolTrimTo(g_pool[d], 0);
+}
+
 lq_status scratch_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
   *p = nullptr;
   if (inject_alloc_failure()) {
@@ -64,7 +106,10 @@ lq_status scratch_alloc(void** p, size_t bytes, cudaStream_t s, const char* what
     return LQ_ERR_OOM;
   }
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  lq_status pst = library_pool(&pool);
+  if (pst != LQ_OK) return pst;
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -366,6 +411,8 @@ lq_status lq_free_all(void) {
     fns = release_list();
   }
   for (auto fn : fns) fn();
+  cudaDeviceSynchronize();
+  trim_pools();
   return LQ_OK;
 }
 

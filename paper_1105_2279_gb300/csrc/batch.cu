@@ -31,7 +31,7 @@ struct MuList4 {
 template <typename R, bool REPRO>
 __global__ void __launch_bounds__(256) k_stout_batch(const BatchDesc* __restrict__ D, int n_cfg, long long n_items,
                                                      unsigned long long* __restrict__ counter, int parity, R rho,
-                                                     unsigned dirs, int nsite, MuList4 ml) {
+                                                     unsigned dirs, int nsite, int nd, MuList4 ml) {
   typedef typename vec2<R>::type V2;
   __shared__ long long item_s;
   for (;;) {
@@ -48,9 +48,11 @@ __global__ void __launch_bounds__(256) k_stout_batch(const BatchDesc* __restrict
     }
     const GeomArgs g = D[lo].g;
     const long long local = item - D[lo].item_begin;
-    const int tpd = D[lo].tiles_per_dir;
-    const int mu = ml.mu[(int)(local / tpd)];
-    const long long tile = local % tpd;
+    // the smeared directions of one tile are consecutive items, so the
+    // direction sweeps of a tile share cached lines
+    const int mi = (int)(local % nd);
+    const long long tile = local / nd;
+    const int mu = mi == 0 ? ml.mu[0] : (mi == 1 ? ml.mu[1] : (mi == 2 ? ml.mu[2] : ml.mu[3]));
     const V2* in = (const V2*)(parity ? D[lo].b : D[lo].a);
     V2* out = (V2*)(parity ? D[lo].a : D[lo].b);
     const long long V = g.V;
@@ -138,14 +140,14 @@ static lq_status batch_sequence(lq_field* const* links, int n_cfg, const BatchPl
     unsigned long long* ctr = p.counters + k;
     if (prec == LQ_F64) {
       if (reproject)
-        k_stout_batch<double, true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, ml);
+        k_stout_batch<double, true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, nd, ml);
       else
-        k_stout_batch<double, false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, ml);
+        k_stout_batch<double, false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, nd, ml);
     } else {
       if (reproject)
-        k_stout_batch<float, true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, ml);
+        k_stout_batch<float, true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, nd, ml);
       else
-        k_stout_batch<float, false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, ml);
+        k_stout_batch<float, false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, nd, ml);
     }
     if ((st = launch_check("k_stout_batch"))) return st;
   }
