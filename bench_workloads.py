@@ -14,7 +14,8 @@
                 vector and 4-spin fermion, FP32; and 24^3 x 48 in FP64.
 * micro16    -- 16^3 x 32, 10 spatial steps rho = 0.1 in FP64, and the fused
                 expression micro-suite on the same field: sum_mu tr(U_mu(x)
-                U_mu(x+mu)), U_mu(x) U_nu(x+mu)^dag, plaquette.
+                U_mu(x+mu)), U_mu(x) U_nu(x+mu)^dag, plaquette; the two
+                programs interpreted and NVRTC-compiled.
 Inputs are resident on the device before timing; times are CUDA events.
 """
 import json
@@ -147,12 +148,16 @@ def micro16(args, torch, lq, fieldgen):
     t_tr = _events(torch, lambda: lq.expr_eval(p_tr, [f], reduce=True), args.steps, args.warmup)
     t_adj = _events(torch, lambda: lq.expr_eval(p_adj, [f], out=out), args.steps, args.warmup)
     t_plaq = _events(torch, lambda: lq.plaquette(f), args.steps, args.warmup)
+    lq.expr_eval_jit(p_tr, [f], reduce=True)          # compile once (not timed)
+    lq.expr_eval_jit(p_adj, [f], out=out)
+    t_tr_jit = _events(torch, lambda: lq.expr_eval_jit(p_tr, [f], reduce=True), args.steps, args.warmup)
+    t_adj_jit = _events(torch, lambda: lq.expr_eval_jit(p_adj, [f], out=out), args.steps, args.warmup)
     links = 10 * V * 3
     return {"metric": "stout link-updates/s (16^3x32, 10 spatial steps, FP64)", "value": links / (t_smear * 1e-3),
             "unit": "link-updates/s", "ms_per_step": t_smear, "dtype": "f64",
             "config": {"workload": "16^3x32, exp(i*0.3*H) links seed 1, 10 stout steps rho=0.1 spatial"},
             "micro_suite_ms": {"trace_sum_mu_tr_UU_shift": t_tr, "shifted_adjoint_product": t_adj,
-                               "plaquette": t_plaq},
+                               "plaquette": t_plaq, "trace_sum_jit": t_tr_jit, "shifted_adjoint_product_jit": t_adj_jit},
             "micro_suite_gb_s": {"trace_sum": V * 4 * 2 * 144 / (t_tr * 1e-3) / 1e9 / 2,
                                  "shifted_adjoint_product": V * (2 * 144 + 144) / (t_adj * 1e-3) / 1e9}}
 

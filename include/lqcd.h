@@ -151,6 +151,34 @@ lq_status lq_expr_eval(lq_field* out_or_null, const lq_op* prog, int n_ops,
                        const lq_field* const* operands, int n_operands,
                        double* reduce_out_or_null, void* stream);
 
+/* JIT-compiled form of lq_expr_eval ([W] Sec. 4.1: one kernel compiled per
+ * expression at run time and kept loaded; Sec. 8: compiled once across
+ * runs).  The program becomes straight-line CUDA C (registers as locals,
+ * kinds and shifts as constants) compiled by NVRTC for sm_103a; the cubin is
+ * cached in memory per program text and device, and on disk when
+ * lq_jit_cache_dir() names a directory.  Same arguments, validation and
+ * results (bit for bit) as lq_expr_eval.  Returns LQ_ERR_UNSUPPORTED if
+ * libnvrtc cannot be loaded; compilation errors come back as LQ_ERR_CUDA with
+ * the NVRTC log in lq_last_error(). */
+lq_status lq_expr_eval_jit(lq_field* out_or_null, const lq_op* prog, int n_ops,
+                           const lq_field* const* operands, int n_operands,
+                           double* reduce_out_or_null, void* stream);
+
+/* Compiles (or finds in the caches) the kernel lq_expr_eval_jit would run for
+ * this program, fields and reduction flag, without launching anything: the
+ * "compile before production" step.  Needs no GPU. */
+lq_status lq_expr_jit_prepare(const lq_field* out_or_null, const lq_op* prog, int n_ops,
+                              const lq_field* const* operands, int n_operands, int reduce);
+
+/* Directory for compiled expression kernels kept across runs (NULL or ""
+ * disables the disk cache).  Files: lqjit_<hash>.cu (the source, compared on
+ * lookup) and lqjit_<hash>.cubin. */
+lq_status lq_jit_cache_dir(const char* path);
+
+/* out[0..3] = NVRTC compilations, in-memory cache hits, disk cache hits,
+ * module loads, since the library was loaded. */
+lq_status lq_jit_stats(long long out[4]);
+
 /* ---- global reductions (FP64 accumulation, deterministic) ---------------- */
 
 /* out[0..1] = sum over sites and components (re, im); REAL fields give im = 0. */

@@ -181,6 +181,35 @@ def expr_eval(prog, operands, out=None, reduce=False, stream=None):
     return complex(red[0], red[1]) if reduce else None
 
 
+def expr_eval_jit(prog, operands, out=None, reduce=False, stream=None):
+    """expr_eval through an NVRTC-compiled kernel (lq_expr_eval_jit)."""
+    arr, n = compile_program(prog)
+    hs = (c_void_p * len(operands))(*[f.handle for f in operands])
+    red = (c_double * 2)()
+    _check(L.load().lq_expr_eval_jit(out.handle if out is not None else None, arr, n, hs, len(operands),
+                                     red if reduce else None, _stream(stream)), "lq_expr_eval_jit")
+    return complex(red[0], red[1]) if reduce else None
+
+
+def expr_jit_prepare(prog, operands, out=None, reduce=False):
+    """Compiles (or finds cached) the JIT kernel of a program without launching it."""
+    arr, n = compile_program(prog)
+    hs = (c_void_p * len(operands))(*[f.handle for f in operands])
+    _check(L.load().lq_expr_jit_prepare(out.handle if out is not None else None, arr, n, hs, len(operands),
+                                        int(bool(reduce))), "lq_expr_jit_prepare")
+
+
+def jit_cache_dir(path=None):
+    _check(L.load().lq_jit_cache_dir(path.encode() if path else None), "lq_jit_cache_dir")
+
+
+def jit_stats():
+    """(NVRTC compilations, memory hits, disk hits, module loads)."""
+    out = (ctypes.c_longlong * 4)()
+    _check(L.load().lq_jit_stats(out), "lq_jit_stats")
+    return tuple(out)
+
+
 def reduce_sum(f, stream=None):
     r = (c_double * 2)()
     _check(L.load().lq_reduce_sum(f.handle, r, _stream(stream)), "lq_reduce_sum")

@@ -46,6 +46,10 @@ SIGNATURES = {
     "lq_field_download": (c_int, [_P, _P, _P]),
     "lq_shift": (c_int, [_P, _P, c_int, c_int, _P]),
     "lq_expr_eval": (c_int, [_P, POINTER(LqOp), c_int, POINTER(_P), c_int, POINTER(c_double), _P]),
+    "lq_expr_eval_jit": (c_int, [_P, POINTER(LqOp), c_int, POINTER(_P), c_int, POINTER(c_double), _P]),
+    "lq_expr_jit_prepare": (c_int, [_P, POINTER(LqOp), c_int, POINTER(_P), c_int, c_int]),
+    "lq_jit_cache_dir": (c_int, [ctypes.c_char_p]),
+    "lq_jit_stats": (c_int, [POINTER(ctypes.c_longlong)]),
     "lq_reduce_sum": (c_int, [_P, POINTER(c_double), _P]),
     "lq_reduce_trace": (c_int, [_P, POINTER(c_double), _P]),
     "lq_plaquette": (c_int, [_P, POINTER(c_double), _P]),

@@ -53,8 +53,32 @@ def _stale(objs_srcs, lib):
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+JIT_PRELUDE_PARTS = ("geom.cuh", "su3.cuh", "expr_ops.cuh", "reduce.cuh")
+JIT_PRELUDE = os.path.join(CSRC, "jit_prelude.inc")
+
+
+def write_jit_prelude():
+    """Embeds the NVRTC-compatible device headers as one raw string literal for
+    the JIT (csrc/jit.cu); rewritten only when its content changes."""
+    parts = []
+    for name in JIT_PRELUDE_PARTS:
+        with open(os.path.join(CSRC, name)) as f:
+            lines = [ln for ln in f.read().splitlines()
+                     if not ln.startswith('#include "') and ln.strip() != "#pragma once"]
+        parts.append("\n".join(lines))
+    text = 'R"LQJIT(\n' + "\n".join(parts) + '\n)LQJIT"\n'
+    old = None
+    if os.path.exists(JIT_PRELUDE):
+        with open(JIT_PRELUDE) as f:
+            old = f.read()
+    if old != text:
+        with open(JIT_PRELUDE, "w") as f:
+            f.write(text)
+
+
 def build_library(force=False, verbose_ptxas=False, jobs=None):
     """Compiles and links liblqcd.so if any source is newer; returns its path."""
+    write_jit_prelude()
     if not force and not verbose_ptxas and not _stale(None, LIB):
         return LIB
     os.makedirs(BUILD, exist_ok=True)

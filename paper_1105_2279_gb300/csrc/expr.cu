@@ -8,9 +8,14 @@
 // index arithmetic instead of tables.
 #include <cstring>
 
+#include "expr_ops.cuh"
 #include "lq_internal.h"
 #include "reduce.cuh"
 #include "stout_core.cuh"
+
+static_assert(lq::kKindLinks == LQ_LINKS && lq::kKindMatrix == LQ_COLOR_MATRIX && lq::kKindVector == LQ_COLOR_VECTOR &&
+                  lq::kKindComplex == LQ_COMPLEX && lq::kKindReal == LQ_REAL,
+              "field kind numbering");
 
 namespace lq {
 
@@ -41,54 +46,6 @@ struct DevProg {
   const void* operand[LQ_EXPR_MAX_OPERANDS];
   int operand_kind[LQ_EXPR_MAX_OPERANDS];
 };
-
-template <typename R>
-__device__ __forceinline__ M3<R> load_operand(const void* base, int kind, int dir, long long V, int s) {
-  typedef typename vec2<R>::type V2;
-  M3<R> m;
-  m_zero(m);
-  if (kind == LQ_LINKS || kind == LQ_COLOR_MATRIX) {
-    m = ld_m3<R>((const V2*)base + (long long)dir * 9 * V + s, V);
-  } else if (kind == LQ_COLOR_VECTOR) {
-    const V2* p = (const V2*)base + s;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      V2 v = __ldg(p + r * V);
-      m.e[3 * r] = mkc<R>(v.x, v.y);
-    }
-  } else if (kind == LQ_COMPLEX) {
-    V2 v = __ldg((const V2*)base + s);
-    m.e[0] = m.e[4] = m.e[8] = mkc<R>(v.x, v.y);
-  } else {
-    R v = __ldg((const R*)base + s);
-    m.e[0] = m.e[4] = m.e[8] = mkc<R>(v, 0);
-  }
-  return m;
-}
-
-template <typename R>
-__device__ __forceinline__ void store_result(void* base, int kind, long long V, int s, const M3<R>& m) {
-  typedef typename vec2<R>::type V2;
-  if (kind == LQ_COLOR_MATRIX) {
-    st_m3<R>((V2*)base + s, V, m);
-  } else if (kind == LQ_COLOR_VECTOR) {
-    V2* p = (V2*)base + s;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      V2 v;
-      v.x = m.e[3 * r].re;
-      v.y = m.e[3 * r].im;
-      p[r * V] = v;
-    }
-  } else if (kind == LQ_COMPLEX) {
-    V2 v;
-    v.x = m.e[0].re;
-    v.y = m.e[0].im;
-    ((V2*)base)[s] = v;
-  } else {
-    ((R*)base)[s] = m.e[0].re;
-  }
-}
 
 template <typename R>
 __global__ void __launch_bounds__(kReduceThreads) k_expr(DevProg prog, GeomArgs g, void* out, int out_kind,
@@ -182,52 +139,46 @@ extern "C" lq_status lq_shift(lq_field* out, const lq_field* in, int mu, int sig
   return launch_check("lq_shift");
 }
 
-extern "C" lq_status lq_expr_eval(lq_field* out, const lq_op* prog, int n_ops, const lq_field* const* operands,
-                                  int n_operands, double* reduce_out, void* stream) {
-  clear_error();
+namespace lq {
+
+// Checks a program and its fields for lq_expr_eval / lq_expr_eval_jit / lq_expr_jit_prepare.
+lq_status expr_validate(const lq_field* out, const lq_op* prog, int n_ops, const lq_field* const* operands,
+                        int n_operands, bool reduce, const char* who) {
   if (!prog || n_ops < 1 || n_ops > LQ_EXPR_MAX_OPS || !operands || n_operands < 1 ||
       n_operands > LQ_EXPR_MAX_OPERANDS) {
-    set_error("lq_expr_eval: need 1..%d ops and 1..%d operands", LQ_EXPR_MAX_OPS, LQ_EXPR_MAX_OPERANDS);
+    set_error("%s: need 1..%d ops and 1..%d operands", who, LQ_EXPR_MAX_OPS, LQ_EXPR_MAX_OPERANDS);
     return LQ_ERR_ARG;
   }
-  if (!out && !reduce_out) {
-    set_error("lq_expr_eval: neither an output field nor a reduction was requested");
+  if (!out && !reduce) {
+    set_error("%s: neither an output field nor a reduction was requested", who);
     return LQ_ERR_ARG;
   }
   const lq_field* f0 = operands[0];
   for (int k = 0; k < n_operands; ++k) {
     if (!operands[k]) {
-      set_error("lq_expr_eval: operand %d is NULL", k);
+      set_error("%s: operand %d is NULL", who, k);
       return LQ_ERR_ARG;
     }
     if (!same_geom(operands[k]->geom, f0->geom) || operands[k]->prec != f0->prec) {
-      set_error("lq_expr_eval: operand %d differs in geometry or precision", k);
+      set_error("%s: operand %d differs in geometry or precision", who, k);
       return LQ_ERR_GEOM;
     }
     if (operands[k]->kind == LQ_FERMION) {
-      set_error("lq_expr_eval: FERMION operands are not supported by the 3x3 register machine");
+      set_error("%s: FERMION operands are not supported by the 3x3 register machine", who);
       return LQ_ERR_UNSUPPORTED;
     }
   }
   if (out) {
     if (!same_geom(out->geom, f0->geom) || out->prec != f0->prec || out->kind == LQ_LINKS ||
         out->kind == LQ_FERMION) {
-      set_error("lq_expr_eval: output must share geometry/precision and not be LQ_LINKS or LQ_FERMION");
+      set_error("%s: output must share geometry/precision and not be LQ_LINKS or LQ_FERMION", who);
       return LQ_ERR_GEOM;
     }
     for (int k = 0; k < n_operands; ++k)
       if (operands[k]->ptr == out->ptr) {
-        set_error("lq_expr_eval: output aliases operand %d", k);
+        set_error("%s: output aliases operand %d", who, k);
         return LQ_ERR_ARG;
       }
-  }
-  DevProg dp;
-  std::memset(&dp, 0, sizeof(dp));
-  dp.n_ops = n_ops;
-  dp.n_operands = n_operands;
-  for (int k = 0; k < n_operands; ++k) {
-    dp.operand[k] = operands[k]->ptr;
-    dp.operand_kind[k] = operands[k]->kind;
   }
   for (int i = 0; i < n_ops; ++i) {
     const lq_op& o = prog[i];
@@ -242,10 +193,34 @@ extern "C" lq_status lq_expr_eval(lq_field* out, const lq_op* prog, int n_ops, c
       ok = o.a >= 0 && o.a < n_operands && o.sign >= -1 && o.sign <= 1 && (o.sign == 0 || (o.mu >= 0 && o.mu <= 3));
       if (ok) ok = operands[o.a]->kind == LQ_LINKS ? (o.dir >= 0 && o.dir < 4) : true;
     }
+    if (ok && o.code == LQ_OP_SCALE) ok = o.re == o.re && o.im == o.im;
     if (!ok) {
-      set_error("lq_expr_eval: op %d (code %d) is malformed", i, o.code);
+      set_error("%s: op %d (code %d) is malformed", who, i, o.code);
       return LQ_ERR_ARG;
     }
+  }
+  return LQ_OK;
+}
+
+}  // namespace lq
+
+extern "C" lq_status lq_expr_eval(lq_field* out, const lq_op* prog, int n_ops, const lq_field* const* operands,
+                                  int n_operands, double* reduce_out, void* stream) {
+  clear_error();
+  lq_status st = expr_validate(out, prog, n_ops, operands, n_operands, reduce_out != nullptr, "lq_expr_eval");
+  if (st != LQ_OK) return st;
+  const lq_field* f0 = operands[0];
+  DevProg dp;
+  std::memset(&dp, 0, sizeof(dp));
+  dp.n_ops = n_ops;
+  dp.n_operands = n_operands;
+  for (int k = 0; k < n_operands; ++k) {
+    dp.operand[k] = operands[k]->ptr;
+    dp.operand_kind[k] = operands[k]->kind;
+  }
+  for (int i = 0; i < n_ops; ++i) {
+    const lq_op& o = prog[i];
+    const bool uses_b = o.code == LQ_OP_MUL || o.code == LQ_OP_ADD || o.code == LQ_OP_SUB;
     DevOp d;
     d.code = (signed char)o.code;
     d.dst = (signed char)(o.code == LQ_OP_STORE ? 0 : o.dst);
@@ -265,7 +240,6 @@ extern "C" lq_status lq_expr_eval(lq_field* out, const lq_op* prog, int n_ops, c
   void* outp = out ? out->ptr : nullptr;
   const int out_kind = out ? out->kind : LQ_COLOR_MATRIX;
   double* scratch = nullptr;
-  lq_status st;
   if (reduce_out) {
     st = scratch_alloc((void**)&scratch, sizeof(double) * 2 * (grid + 1), s, "lq_expr_eval");
     if (st != LQ_OK) return st;

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "../../include/lqcd.h"
+#include "geom.cuh"
 
 struct lq_geom {
   int dims[4];
@@ -67,12 +68,6 @@ int current_device();
 lq_status scratch_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
 void scratch_free(void* p, cudaStream_t s);
 
-// Geometry parameters passed to kernels by value.
-struct GeomArgs {
-  int L[4];
-  int stride[4];   // 1, Lx, Lx*Ly, Lx*Ly*Lz
-  int V;
-};
 inline GeomArgs geom_args(const lq_geom& g) {
   GeomArgs a;
   int st = 1;

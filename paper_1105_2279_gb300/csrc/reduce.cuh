@@ -4,7 +4,9 @@
 // size, so results are bit-identical run to run.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
 namespace lq {
 
@@ -48,6 +50,7 @@ template <int NV> __global__ void k_reduce_partials(const double* __restrict__ p
   block_sum_store<NV>(v, out);
 }
 
+#ifndef __CUDACC_RTC__
 // Grid size of a reducing kernel over n items: a function of n only (the cap
 // is 8 blocks of 256 threads on each of the 152 SMs of a GB300).
 constexpr int kReduceMaxBlocks = 1216;
@@ -57,5 +60,6 @@ inline int reduce_grid(long long n) {
   if (b < 1) b = 1;
   return (int)b;
 }
+#endif
 
 }  // namespace lq

@@ -2,7 +2,9 @@
 // multiply-accumulate).  Header-only so every kernel inlines it into registers.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 
 namespace lq {
 

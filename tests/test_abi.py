@@ -119,3 +119,36 @@ def test_injected_allocation_failure_is_reported(lqlib, monkeypatch):
     assert lib.lq_stout_backward(h, 0.1, 1, 15, None, 6.0, h, None, None, None) in (-1, -3)
     monkeypatch.delenv("LQ_FAULT_INJECT")
     lib.lq_field_free(h)
+
+
+def test_jit_compiles_and_caches_without_a_gpu(lqlib, tmp_path):
+    """lq_expr_jit_prepare generates and NVRTC-compiles a program's kernel on the
+    host (no device needed); the second request hits the in-memory cache; after
+    lq_free_all drops that cache, the cubin comes back from the disk cache."""
+    lib = lqlib.capi()
+    g = lqlib.Geometry((4, 3, 4, 5))
+    h = ctypes.c_void_p()
+    assert lib.lq_field_wrap(g.handle, 0, 0, ctypes.c_void_p(0x1000), 1 << 26, ctypes.byref(h)) == 0
+
+    class _F:
+        handle = h
+    prog = [("loadl", 0, 0, 3, 0, 0), ("loadl", 1, 0, 0, 3, -1), ("mul", 2, 0, 1), ("trace", 3, 2),
+            ("scale", 3, 3, 0.375, -1.25), ("store", 3)]
+    lqlib.jit_cache_dir(str(tmp_path))
+    c0 = lqlib.jit_stats()
+    lqlib.expr_jit_prepare(prog, [_F], reduce=True)
+    c1 = lqlib.jit_stats()
+    assert c1[0] == c0[0] + 1
+    lqlib.expr_jit_prepare(prog, [_F], reduce=True)
+    assert lqlib.jit_stats()[1] == c1[1] + 1
+    assert any(p.suffix == ".cubin" for p in tmp_path.iterdir())
+    lqlib.free_all()
+    lqlib.expr_jit_prepare(prog, [_F], reduce=True)
+    c3 = lqlib.jit_stats()
+    assert c3[2] == c1[2] + 1 and c3[0] == c1[0]
+    lqlib.jit_cache_dir(None)
+    # malformed programs are refused before any code generation
+    bad, n = lqlib.compile_program([("loadl", 0, 0, 9, 0, 0), ("store", 0)])
+    ops = (ctypes.c_void_p * 1)(h)
+    assert lib.lq_expr_jit_prepare(None, bad, n, ops, 1, 1) == -1
+    lib.lq_field_free(h)

@@ -154,3 +154,40 @@ def test_jacobi_hopping_term_program(gpu):
     lq.expr_eval(prog, [fU, fchi], out=out)
     ref = expr.jacobi_smear(U, chi, kappa, 1, 1.0)
     assert np.max(np.abs(out.download() - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_jit_programs_bit_identical_to_interpreter(gpu, prec):
+    """NVRTC-compiled programs (lq_expr_eval_jit) give bit-identical fields and
+    reductions to the interpreted ones, for every output kind."""
+    dims = (5, 4, 3, 6)
+    U = fieldgen.near_identity_su3(dims, 209)
+    chi = fieldgen.color_vector(dims, 210)
+    g = lq.Geometry(dims)
+    fU = upload_links(U, prec)
+    fchi = lq.Field.from_host(g, lq.LQ_COLOR_VECTOR, prec, chi)
+    p_tr, p_adj = micro_suite_programs()
+    assert lq.expr_eval_jit(p_tr, [fU], reduce=True) == lq.expr_eval(p_tr, [fU], reduce=True)
+    for p in p_adj:
+        a, b = lq.Field(g, lq.LQ_COLOR_MATRIX, prec), lq.Field(g, lq.LQ_COLOR_MATRIX, prec)
+        ra = lq.expr_eval_jit(p, [fU], out=a, reduce=True)
+        rb = lq.expr_eval(p, [fU], out=b, reduce=True)
+        assert ra == rb and np.array_equal(a.download(), b.download())
+    hop = [("loadl", 0, 0, 2, 0, 0), ("load", 1, 1, 2, +1), ("mul", 2, 0, 1), ("loadl", 3, 0, 2, 2, -1),
+           ("adj", 3, 3), ("load", 4, 1, 2, -1), ("mul", 5, 3, 4), ("add", 2, 2, 5),
+           ("scale", 2, 2, 0.21, 0.0), ("load", 6, 1, 0, 0), ("add", 2, 2, 6), ("store", 2)]
+    a, b = lq.Field(g, lq.LQ_COLOR_VECTOR, prec), lq.Field(g, lq.LQ_COLOR_VECTOR, prec)
+    lq.expr_eval_jit(hop, [fU, fchi], out=a)
+    lq.expr_eval(hop, [fU, fchi], out=b)
+    assert np.array_equal(a.download(), b.download())
+    for kind, prog in ((lq.LQ_COMPLEX, [("loadl", 0, 0, 1, 3, -1), ("trace", 1, 0), ("store", 1)]),
+                       (lq.LQ_REAL, [("loadl", 0, 0, 0, 0, 0), ("loadl", 1, 0, 3, 0, +1), ("mul", 2, 0, 1),
+                                     ("retr", 3, 2), ("store", 3)])):
+        a, b = lq.Field(g, kind, prec), lq.Field(g, kind, prec)
+        lq.expr_eval_jit(prog, [fU], out=a)
+        lq.expr_eval(prog, [fU], out=b)
+        assert np.array_equal(a.download(), b.download())
+    before = lq.jit_stats()
+    lq.expr_eval_jit(p_tr, [fU], reduce=True)          # cached: no new compilation or module load
+    after = lq.jit_stats()
+    assert after[0] == before[0] and after[3] == before[3] and after[1] == before[1] + 1

@@ -183,3 +183,60 @@ def test_48c96_six_steps_sampled(gpu, prec):
         worst = max(worst, float(np.max(np.abs(got[c[3], c[2], c[1], c[0]].astype(np.complex128) - ref))))
     tol = F64_TOL if prec == lq.LQ_F64 else F32_TOL_PER_STEP * n
     assert worst <= tol, worst
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1, 1), (1, 2, 1, 3), (2, 1, 1, 1), (1, 1, 5, 1)])
+def test_degenerate_extents(gpu, dims):
+    """Extents of 1 (x + mu = x - mu = x) and 2 in every combination."""
+    U = fieldgen.haar_su3(dims, 109)
+    ref = stout.stout_smear(U, 0.1, 2, ALL)
+    got = _run(U, lq.LQ_F64, 0.1, 2, ALL)
+    assert np.max(np.abs(got - ref)) <= F64_TOL
+    f = upload_links(U, lq.LQ_F64)
+    assert np.allclose(lq.plaquette(f), gauge.plaquette(U), rtol=0, atol=1e-14)
+
+
+def _pure_gauge_links(dims, prec, seed):
+    """U_mu(x) = g(x) g(x+mu)^dag with g(x) = diag(e^{i phi}, e^{-i phi}, 1), built on the
+    device in the [dir][comp][site][re,im] layout; returns (tensor, field)."""
+    import torch
+    lx, ly, lz, lt = dims
+    dt = torch.float64 if prec == lq.LQ_F64 else torch.float32
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    phi = (torch.rand((lt, lz, ly, lx), generator=gen, device="cuda", dtype=torch.float64) * 6.283185307179586)
+    V = lx * ly * lz * lt
+    t = torch.zeros((4, 9, V, 2), dtype=dt, device="cuda")
+    for mu, axis in enumerate((3, 2, 1, 0)):
+        d = (phi - torch.roll(phi, -1, dims=axis)).reshape(-1)
+        c, s = torch.cos(d).to(dt), torch.sin(d).to(dt)
+        t[mu, 0, :, 0], t[mu, 0, :, 1] = c, s
+        t[mu, 4, :, 0], t[mu, 4, :, 1] = c, -s
+        t[mu, 8, :, 0] = 1
+        del d, c, s
+    del phi
+    g = lq.Geometry(dims)
+    return t, lq.Field(g, lq.LQ_LINKS, prec, tensor=t)
+
+
+@pytest.mark.parametrize("prec,dims", [(lq.LQ_F32, (128, 128, 128, 128)), (lq.LQ_F64, (128, 128, 128, 64))])
+def test_largest_volumes_pure_gauge_fixed_point(gpu, prec, dims):
+    """2^28 sites (FP32, 77 GB of links) and 2^27 sites (FP64, 77 GB): with the
+    library's double buffer these are the largest powers of two that fit in HBM,
+    and element offsets exceed 2^32.  A pure-gauge field is a fixed point of stout
+    smearing (every staple equals U_mu(x), so Q = 0), has plaquette 1, and any wrong
+    neighbour index would break both."""
+    import torch
+    t, f = _pure_gauge_links(dims, prec, 7)
+    ref_planes = [t[mu, c].clone() for mu, c in ((0, 0), (3, 4))]
+    lq.stout_smear(f, 0.1, 2, ALL)
+    tol = 2e-6 if prec == lq.LQ_F32 else 1e-13
+    for (mu, c), ref in zip(((0, 0), (3, 4)), ref_planes):
+        assert torch.max(torch.abs(t[mu, c] - ref)).item() <= tol
+    del ref_planes
+    for mu in range(4):   # off-diagonal components stay exactly zero
+        assert torch.count_nonzero(t[mu, 1]).item() == 0 and torch.count_nonzero(t[mu, 6]).item() == 0
+    p = lq.plaquette(f)
+    assert abs(p[0] - 1.0) <= (1e-6 if prec == lq.LQ_F32 else 1e-13)
+    del f, t
+    torch.cuda.empty_cache()
+    lq.free_all()
