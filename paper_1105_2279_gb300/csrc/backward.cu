@@ -64,8 +64,9 @@ __global__ void __launch_bounds__(128) k_bwd_link(const V2<R>* __restrict__ U, c
   const M3<R> C = m_rscale(staple_sum<R>(U, g, s, c, mu, dirs), rho);
   const M3<R> Umu = ld_m3<R>(U + off, V);
   const QH<R> q = q_from_omega(mul_nd(C, Umu));
-  const CHDeriv d = ch_coefficients_deriv((double)q.d0, (double)q.d1, (double)q.d2, mkc<double>(q.o01.re, q.o01.im),
-                                          mkc<double>(q.o02.re, q.o02.im), mkc<double>(q.o12.re, q.o12.im));
+  const CHDeriv d = ch_coefficients_deriv<sizeof(R) == 4 ? 1 : 2>(
+      to_f64(q.d0), to_f64(q.d1), to_f64(q.d2), mkc(to_f64(q.o01.re), to_f64(q.o01.im)),
+      mkc(to_f64(q.o02.re), to_f64(q.o02.im)), mkc(to_f64(q.o12.re), to_f64(q.o12.im)));
   const QH<R> q2 = q_square(q);
   const M3<R> Qf = qh_full(q), Q2f = qh_full(q2);
   const M3<R> Gpm = ld_m3<R>(Gp + off, V);
@@ -75,24 +76,26 @@ __global__ void __launch_bounds__(128) k_bwd_link(const V2<R>* __restrict__ U, c
   const cx<R> t1 = tr_dn(GE, Qf);
   const cx<R> t2 = tr_dn(GE, Q2f);
   cx<double> a1 = mkc(0.0, 0.0), a2 = mkc(0.0, 0.0);
-  const cx<double> td[3] = {mkc<double>(t0.re, t0.im), mkc<double>(t1.re, t1.im), mkc<double>(t2.re, t2.im)};
+  const cx<double> td[3] = {mkc(to_f64(t0.re), to_f64(t0.im)), mkc(to_f64(t1.re), to_f64(t1.im)),
+                            mkc(to_f64(t2.re), to_f64(t2.im))};
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     a1 = cfma(d.b1[j], td[j], a1);
     a2 = cfma(d.b2[j], td[j], a2);
   }
-  const cx<R> f1 = mkc<R>((R)d.f[1].re, (R)d.f[1].im), f2 = mkc<R>((R)d.f[2].re, (R)d.f[2].im);
+  const cx<R> f1 = mkc<R>(from_f64<R>(d.f[1].re), from_f64<R>(d.f[1].im));
+  const cx<R> f2 = mkc<R>(from_f64<R>(d.f[2].re), from_f64<R>(d.f[2].im));
   const M3<R> H = m_adj(GE);  // G_E^dag
   // M = a1 Q + a2 Q^2 + f1 H + f2 (Q H + H Q)
   M3<R> M = m_add(mul_nn(Qf, H), mul_nn(H, Qf));
   M = m_scale(M, f2);
   m_addto(M, m_scale(H, f1));
-  m_addto(M, m_scale(Qf, mkc<R>((R)a1.re, (R)a1.im)));
-  m_addto(M, m_scale(Q2f, mkc<R>((R)a2.re, (R)a2.im)));
+  m_addto(M, m_scale(Qf, mkc<R>(from_f64<R>(a1.re), from_f64<R>(a1.im))));
+  m_addto(M, m_scale(Q2f, mkc<R>(from_f64<R>(a2.re), from_f64<R>(a2.im))));
   // G_Omega = TA(i M^dag)
   const M3<R> GO = m_ta(m_scale(m_adj(M), mkc<R>(0, 1)));
   // E = exp(iQ) and the local gradient E^dag G' + G_Omega^dag C
-  const M3<R> E = expiq_assemble(q, q2, mkc<R>((R)d.f[0].re, (R)d.f[0].im), f1, f2);
+  const M3<R> E = expiq_assemble(q, q2, mkc<R>(from_f64<R>(d.f[0].re), from_f64<R>(d.f[0].im)), f1, f2);
   M3<R> Gl = mul_dn(E, Gpm);
   mac_dn(Gl, GO, C);
   st_m3<R>(Gout + off, V, Gl);

@@ -118,6 +118,20 @@ __device__ __forceinline__ void cos_sinc_from_sq(double w2, double* cw, double* 
   *cw = fma(w2, pc, 1.0);
 }
 
+// xi1(w) = cos(w)/w^2 - sin(w)/w^3 = xi0'(w)/w from w^2, for w^2 <= (pi/4)^2:
+// sum_j (-1)^(j+1) (2j+2) w^(2j) / (2j+3)!, truncated after j = 7 (next term
+// < 1e-15 relative).
+__device__ __forceinline__ double xi1_from_sq(double w2) {
+  double p = 16.0 / 355687428096000.0;    // +16/17!
+  p = fma(p, w2, -14.0 / 1307674368000.0);  // -14/15!
+  p = fma(p, w2, 12.0 / 6227020800.0);      // +12/13!
+  p = fma(p, w2, -10.0 / 39916800.0);       // -10/11!
+  p = fma(p, w2, 8.0 / 362880.0);           // +8/9!
+  p = fma(p, w2, -6.0 / 5040.0);            // -6/7!
+  p = fma(p, w2, 4.0 / 120.0);              // +4/5!
+  return fma(p, w2, -2.0 / 6.0);            // -2/3!
+}
+
 // sin and cos of any finite x: reduction x = k pi/2 + r with pi/2 split in two
 // doubles (Cody & Waite, "Software Manual for the Elementary Functions",
 // 1980) and a fused multiply-add per part, then the quadrant of k.  Used for

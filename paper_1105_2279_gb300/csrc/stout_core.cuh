@@ -169,6 +169,7 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
 struct CHDeriv {
   cx<double> f[3], b1[3], b2[3];
 };
+template <int NR = 2>
 __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, double d2, cx<double> o01,
                                                          cx<double> o02, cx<double> o12) {
   CHDeriv r;
@@ -196,27 +197,28 @@ __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, d
     return r;
   }
   const bool neg = c0 < 0.0;
-  const double s3 = sqrt(c1 * (1.0 / 3.0));
-  const double c0max = 2.0 * s3 * s3 * s3;
-  const double x = fmin(fabs(c0) / c0max, 1.0);
-  const double theta = acos(x);
-  double st, ct;
-  sincos(theta * (1.0 / 3.0), &st, &ct);
-  const double u = s3 * ct;
-  const double w = sqrt(c1) * st;
-  const double u2 = u * u, w2 = w * w;
-  double sw, cw;
-  sincos(w, &sw, &cw);
-  double xi0, xi1;
-  if (fabs(w) <= LQ_XI0_SERIES) {
-    xi0 = 1.0 - w2 * (1.0 / 6.0) * (1.0 - w2 * (1.0 / 20.0) * (1.0 - w2 * (1.0 / 42.0)));
-    xi1 = -1.0 / 3.0 + w2 * (1.0 / 30.0) * (1.0 - w2 * (1.0 / 28.0) * (1.0 - w2 * (1.0 / 54.0)));
+  // same reductions as ch_coefficients (fp64_math.cuh)
+  const double a = c1 * (1.0 / 3.0);
+  const double r3 = rsqrt_nr<NR>(a);
+  const double s3 = a * r3;
+  const double x = fmin(0.5 * fabs(c0) * (r3 * r3 * r3), 1.0);
+  const double y = cos_third_acos<NR>(x);
+  const double u = s3 * y;
+  const double u2 = u * u;
+  const double w2 = fmax(c1 * ((1.0 - y) * (1.0 + y)), 0.0);
+  double cw, xi0, xi1;
+  if (w2 <= 0.61685027506808491) {  // w <= pi/4
+    cos_sinc_from_sq(w2, &cw, &xi0);
+    xi1 = xi1_from_sq(w2);
   } else {
-    xi0 = sw / w;
-    xi1 = (cw - xi0) / w2;
+    const double rw = rsqrt_nr<NR>(w2);
+    double sw;
+    sincos_red(w2 * rw, &sw, &cw);
+    xi0 = sw * rw;
+    xi1 = (cw - xi0) * (rw * rw);
   }
   double su, cu;
-  sincos(u, &su, &cu);
+  sincos_red(u, &su, &cu);
   const cx<double> emiu = mkc(cu, -su);
   const cx<double> e2iu = mkc(cu * cu - su * su, 2.0 * su * cu);
   const cx<double> I = mkc(0.0, 1.0);
@@ -241,7 +243,7 @@ __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, d
   // r2_2 = e^{-iu} [xi0 - 3iu xi1]
   r2[2] = cmul(emiu, mkc(xi0, -3.0 * u * xi1));
   const double D = 9.0 * u2 - w2;
-  const double inv = 1.0 / D;
+  const double inv = rcp_nr<NR>(D);
   const double inv2 = 0.5 * inv * inv;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {

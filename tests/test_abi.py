@@ -152,3 +152,25 @@ def test_jit_compiles_and_caches_without_a_gpu(lqlib, tmp_path):
     ops = (ctypes.c_void_p * 1)(h)
     assert lib.lq_expr_jit_prepare(None, bad, n, ops, 1, 1) == -1
     lib.lq_field_free(h)
+
+
+def test_tuner_cache_file_is_read_back(lqlib, tmp_path):
+    """lq_tune(path) loads a cache written earlier; lq_tune_lookup returns the
+    stored launch shape for its key (kernel, device, precision, dims, dirs).
+    Without a device the device name reads 'unknown'.  Runs in a child process
+    because lq_tune switches the tuner on for the whole process."""
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    path.write_text("stout unknown 1 4 4 4 8 15 64 2 1\nstout unknown 0 6 6 6 12 7 256 8 2\n")
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import paper_1105_2279_gb300 as lq\n"
+        "lq.tune(%r)\n"
+        "assert lq.tune_lookup(lq.LQ_F64, (4, 4, 4, 8), 15) == (64, 2, 1)\n"
+        "assert lq.tune_lookup(lq.LQ_F32, (6, 6, 6, 12), (0, 1, 2)) == (256, 8, 2)\n"
+        "assert lq.tune_lookup(lq.LQ_F32, (4, 4, 4, 8), 15) is None\n"
+        "print('ok')\n" % (ROOT, str(path)))
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120, env=env)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr

@@ -150,3 +150,12 @@ def test_24c48_f32_force_vs_f64(gpu):
     F64, _ = gpu_force(U, lq.LQ_F64, 0.1, 3, ALL)
     F32, _ = gpu_force(U, lq.LQ_F32, 0.1, 3, ALL)
     assert np.max(np.abs(F32.astype(np.complex128) - F64)) <= 6e-5 * np.max(np.abs(F64))
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_force_vanishes_on_unit_field(gpu, prec):
+    """The unit field is a fixed point and a minimum of the Wilson action: the
+    force through the smearing is zero (the Q -> 0 branch of the coefficients)."""
+    U = fieldgen.unit_links((3, 4, 2, 3))
+    F, G = gpu_force(U, prec, 0.1, 2, ALL)
+    assert np.max(np.abs(F)) <= (1e-14 if prec == lq.LQ_F64 else 1e-6)

@@ -191,3 +191,26 @@ def test_jit_programs_bit_identical_to_interpreter(gpu, prec):
     lq.expr_eval_jit(p_tr, [fU], reduce=True)          # cached: no new compilation or module load
     after = lq.jit_stats()
     assert after[0] == before[0] and after[3] == before[3] and after[1] == before[1] + 1
+
+
+def test_library_owned_fields(gpu):
+    """lq_field_alloc / lq_field_device_ptr / lq_field_free through the C ABI:
+    a library-owned field uploads, smears and downloads like a wrapped one."""
+    import ctypes
+    lib = lq.capi()
+    dims = (4, 3, 4, 5)
+    U = fieldgen.near_identity_su3(dims, 211)
+    g = lq.Geometry(dims)
+    h = ctypes.c_void_p()
+    assert lib.lq_field_alloc(g.handle, lq.LQ_LINKS, lq.LQ_F64, None, ctypes.byref(h)) == 0
+    p = ctypes.c_void_p()
+    assert lib.lq_field_device_ptr(h, ctypes.byref(p)) == 0 and p.value
+    host = np.ascontiguousarray(U)
+    assert lib.lq_field_upload(h, ctypes.c_void_p(host.ctypes.data), None) == 0
+    assert lib.lq_stout_smear(h, 0.1, 2, 15, None, None) == 0
+    back = np.empty_like(host)
+    assert lib.lq_field_download(h, ctypes.c_void_p(back.ctypes.data), None) == 0
+    ref = upload_links(U, lq.LQ_F64)
+    lq.stout_smear(ref, 0.1, 2, (0, 1, 2, 3), stream=0)
+    assert np.array_equal(back, ref.download())
+    assert lib.lq_field_free(h) == 0
