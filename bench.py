@@ -40,7 +40,7 @@ METRIC = "stout link-updates/s"
 # flops of the staple / Omega / Q / exp / U' matrix algebra, and of the FP64
 # Cayley-Hamilton coefficients (+ FP64 re-projection in the FP32 path).
 BYTES_PER_LINK = {"f32": 144.0, "f64": 288.0}
-MATRIX_FLOPS_PER_LINK = 3028.0
+MATRIX_FLOPS_PER_LINK = 3019.0
 CH_FLOPS_PER_LINK = 214.0
 REPROJECT_FLOPS_PER_LINK = 142.0
 # GB300 unit counts: 152 SMs x 2 FP64 FMA lanes (304 per cycle) and x 128 FP32 FMA lanes.

@@ -109,6 +109,17 @@ lq_status lq_field_upload(lq_field* f, const void* host_aos, void* stream);
 /* Device SoA -> host AoS ([W] Sec. 5 popFromLattice copy); synchronises. */
 lq_status lq_field_download(const lq_field* f, void* host_aos, void* stream);
 
+/* Field checkpoints on disk (checkpoint / resume of smeared fields).  File:
+ * a 48-byte little-endian header -- magic "LQFIELD1", int32 version (1),
+ * int32 kind, int32 prec, int32 dims[4], int32 0, int64 payload bytes --
+ * followed by the field in the host interchange (AoS) layout.  Save
+ * downloads and writes; load checks the header against the field (dims, kind,
+ * precision: LQ_ERR_GEOM on mismatch, LQ_ERR_ARG for a file that is not a
+ * field checkpoint) before uploading.  Both synchronise `stream`; the host
+ * staging buffer is allocated and freed inside the call. */
+lq_status lq_field_save(const lq_field* f, const char* path, void* stream);
+lq_status lq_field_load(lq_field* f, const char* path, void* stream);
+
 /* ---- site-wise operations ([W] Sec. 6 Listing 1) ------------------------ */
 
 /* out(x) = in(x + sign*mu), periodic: sign = +1 is QDP++ FORWARD, -1

@@ -19,11 +19,38 @@ Op tuples (register indices r*, operand index k):
   ("retr",  rd, ra)           rd = Re tr(ra) * 1
   ("store", ra)               result = ra
 The optional reduction returns sum_x tr(result(x)) as a complex number.
+
+Registers hold 3x3 matrices: an operand that is a colour vector (trailing
+shape (3,)) is loaded into column 0 with the other columns zero, a complex or
+real scalar field (no trailing axes) as scalar * identity; ``as_vector`` and
+``as_scalar`` read a result back the way a vector / scalar output stores it
+(column 0, entry (0,0)).  This is the register machine of the expression
+programs (the flattened expressions of Sec. 4.2).
 """
 import numpy as np
 
 from .lattice import ND, shift
 from .su3 import adj, tr
+
+
+def as_matrix(f):
+    """Promote a site field to 3x3 matrices (vector -> column 0, scalar -> s * 1)."""
+    f = np.asarray(f)
+    if f.ndim == 4:                                   # scalar per site
+        return f[..., None, None] * np.eye(3)
+    if f.shape[-1] == 3 and (f.ndim == 5 or f.shape[-2] != 3):
+        m = np.zeros(f.shape + (3,), dtype=np.complex128)
+        m[..., :, 0] = f
+        return m
+    return f
+
+
+def as_vector(m):
+    return m[..., :, 0]
+
+
+def as_scalar(m):
+    return m[..., 0, 0]
 
 
 def eval_program(prog, operands, nreg=8):
@@ -33,7 +60,7 @@ def eval_program(prog, operands, nreg=8):
         kind = op[0]
         if kind == "load":
             _, rd, k, mu, sign = op
-            f = operands[k]
+            f = as_matrix(operands[k])
             regs[rd] = f if sign == 0 else shift(f, mu, sign)
         elif kind == "loadl":
             _, rd, k, d, mu, sign = op

@@ -132,6 +132,14 @@ class Field:
     def download_ptr(self, host_ptr, stream=None):
         _check(L.load().lq_field_download(self.handle, c_void_p(host_ptr), _stream(stream)), "lq_field_download")
 
+    def save(self, path, stream=None):
+        """lq_field_save: header + AoS payload."""
+        _check(L.load().lq_field_save(self.handle, str(path).encode(), _stream(stream)), "lq_field_save")
+
+    def load(self, path, stream=None):
+        """lq_field_load: refuses files of another geometry, kind or precision."""
+        _check(L.load().lq_field_load(self.handle, str(path).encode(), _stream(stream)), "lq_field_load")
+
     @classmethod
     def from_host(cls, geom, kind, prec, host, device="cuda", stream=None):
         f = cls(geom, kind, prec, device=device)

@@ -44,6 +44,8 @@ SIGNATURES = {
     "lq_field_device_ptr": (c_int, [_P, POINTER(_P)]),
     "lq_field_upload": (c_int, [_P, _P, _P]),
     "lq_field_download": (c_int, [_P, _P, _P]),
+    "lq_field_save": (c_int, [_P, ctypes.c_char_p, _P]),
+    "lq_field_load": (c_int, [_P, ctypes.c_char_p, _P]),
     "lq_shift": (c_int, [_P, _P, c_int, c_int, _P]),
     "lq_expr_eval": (c_int, [_P, POINTER(LqOp), c_int, POINTER(_P), c_int, POINTER(c_double), _P]),
     "lq_expr_eval_jit": (c_int, [_P, POINTER(LqOp), c_int, POINTER(_P), c_int, POINTER(c_double), _P]),

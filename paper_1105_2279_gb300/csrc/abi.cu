@@ -403,6 +403,98 @@ lq_status lq_field_download(const lq_field* f, void* host_aos, void* stream) {
   return st != LQ_OK ? st : st2;
 }
 
+namespace {
+struct FieldFileHeader {
+  char magic[8];
+  int version;
+  int kind;
+  int prec;
+  int dims[4];
+  int reserved;
+  long long bytes;
+};
+static_assert(sizeof(FieldFileHeader) == 48, "checkpoint header is 48 bytes");
+}  // namespace
+
+lq_status lq_field_save(const lq_field* f, const char* path, void* stream) {
+  clear_error();
+  if (!f || !path) {
+    set_error("lq_field_save: NULL argument");
+    return LQ_ERR_ARG;
+  }
+  std::vector<char> host;
+  try {
+    host.resize(f->bytes);
+  } catch (...) {
+    set_error("lq_field_save: host allocation of %zu bytes failed", f->bytes);
+    return LQ_ERR_OOM;
+  }
+  lq_status st = lq_field_download(f, host.data(), stream);
+  if (st != LQ_OK) return st;
+  FieldFileHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "LQFIELD1", 8);
+  h.version = 1;
+  for (int i = 0; i < 4; ++i) h.dims[i] = f->geom.dims[i];
+  h.kind = f->kind;
+  h.prec = f->prec;
+  h.bytes = (long long)f->bytes;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) {
+    set_error("lq_field_save: cannot open %s for writing", path);
+    return LQ_ERR_ARG;
+  }
+  const bool ok = fwrite(&h, sizeof(h), 1, fp) == 1 && fwrite(host.data(), 1, host.size(), fp) == host.size();
+  const bool closed = fclose(fp) == 0;
+  if (!ok || !closed) {
+    set_error("lq_field_save: writing %s failed", path);
+    return LQ_ERR_ARG;
+  }
+  return LQ_OK;
+}
+
+lq_status lq_field_load(lq_field* f, const char* path, void* stream) {
+  clear_error();
+  if (!f || !path) {
+    set_error("lq_field_load: NULL argument");
+    return LQ_ERR_ARG;
+  }
+  FILE* fp = fopen(path, "rb");
+  if (!fp) {
+    set_error("lq_field_load: cannot open %s", path);
+    return LQ_ERR_ARG;
+  }
+  FieldFileHeader h;
+  if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "LQFIELD1", 8) != 0 || h.version != 1) {
+    fclose(fp);
+    set_error("lq_field_load: %s is not a liblqcd field checkpoint", path);
+    return LQ_ERR_ARG;
+  }
+  bool same = h.kind == f->kind && h.prec == f->prec && h.bytes == (long long)f->bytes;
+  for (int i = 0; i < 4; ++i) same = same && h.dims[i] == f->geom.dims[i];
+  if (!same) {
+    fclose(fp);
+    set_error("lq_field_load: %s holds dims %dx%dx%dx%d kind %d prec %d, the field differs", path, h.dims[0],
+              h.dims[1], h.dims[2], h.dims[3], h.kind, h.prec);
+    return LQ_ERR_GEOM;
+  }
+  std::vector<char> host;
+  try {
+    host.resize(f->bytes);
+  } catch (...) {
+    fclose(fp);
+    set_error("lq_field_load: host allocation of %zu bytes failed", f->bytes);
+    return LQ_ERR_OOM;
+  }
+  const bool ok = fread(host.data(), 1, host.size(), fp) == host.size();
+  fclose(fp);
+  if (!ok) {
+    set_error("lq_field_load: %s is truncated", path);
+    return LQ_ERR_ARG;
+  }
+  return lq_field_upload(f, host.data(), stream);
+}
+
 lq_status lq_free_all(void) {
   clear_error();
   std::vector<void (*)()> fns;

@@ -65,6 +65,17 @@ template <typename R> __device__ __forceinline__ QH<R> q_from_omega(const M3<R>&
   return q;
 }
 
+template <typename R> __device__ __forceinline__ QH<R> q_rscale(const QH<R>& q, R s) {
+  QH<R> r;
+  r.d0 = q.d0 * s;
+  r.d1 = q.d1 * s;
+  r.d2 = q.d2 * s;
+  r.o01 = cscale(q.o01, s);
+  r.o02 = cscale(q.o02, s);
+  r.o12 = cscale(q.o12, s);
+  return r;
+}
+
 template <typename R> __device__ __forceinline__ R cnorm2(cx<R> a) { return fmaR(a.re, a.re, a.im * a.im); }
 
 // Q^2 of a compact Hermitian Q, again Hermitian (compact).
@@ -350,9 +361,9 @@ template <typename R> __device__ __forceinline__ M3<R> reproject_via_f64(const M
 // matrix algebra in R; optional FP64 re-projection.
 template <typename R>
 __device__ __forceinline__ M3<R> stout_update(const M3<R>& S, const M3<R>& Umu, R rho, bool reproject) {
-  const M3<R> C = m_rscale(S, rho);
-  const M3<R> Om = mul_nd(C, Umu);
-  const QH<R> q = q_from_omega(Om);
+  // Q is linear in Omega = rho S U^dag: scale the 9 real components of Q
+  // instead of the 18 of the staple sum
+  const QH<R> q = q_rscale(q_from_omega(mul_nd(S, Umu)), rho);
   // FP32 links: one Newton step per FP64 refinement (~1e-13); FP64 links: two
   const CHCoef f = ch_coefficients<sizeof(R) == 4 ? 1 : 2>(to_f64(q.d0), to_f64(q.d1), to_f64(q.d2),
                                    mkc(to_f64(q.o01.re), to_f64(q.o01.im)), mkc(to_f64(q.o02.re), to_f64(q.o02.im)),

@@ -174,3 +174,25 @@ def test_tuner_cache_file_is_read_back(lqlib, tmp_path):
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120, env=env)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr
+
+
+def test_field_checkpoint_header_checks(lqlib, tmp_path):
+    """lq_field_load validates the file before touching the device: a foreign
+    file is LQ_ERR_ARG, a checkpoint of another geometry / kind is LQ_ERR_GEOM."""
+    import struct
+    lib = lqlib.capi()
+    g = lqlib.Geometry((2, 2, 2, 4))
+    h = ctypes.c_void_p()
+    need = lqlib.field_bytes(g, lqlib.LQ_LINKS, lqlib.LQ_F64)
+    assert lib.lq_field_wrap(g.handle, 0, 1, ctypes.c_void_p(0x1000), need, ctypes.byref(h)) == 0
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not a field" * 10)
+    assert lib.lq_field_load(h, str(junk).encode(), None) == -1
+    other = tmp_path / "other.lqf"
+    hdr = b"LQFIELD1" + struct.pack("<iii4iiq", 1, 0, 1, 2, 2, 2, 2, 0, need // 2)
+    assert len(hdr) == 48
+    other.write_bytes(hdr + bytes(need // 2))
+    assert lib.lq_field_load(h, str(other).encode(), None) == -2
+    assert b"differs" in lib.lq_last_error()
+    assert lib.lq_field_load(h, str(tmp_path / "missing.lqf").encode(), None) == -1
+    lib.lq_field_free(h)

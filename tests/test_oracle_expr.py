@@ -101,3 +101,20 @@ def test_jacobi_subset_of_directions_and_fermion():
     both = expr.jacobi_smear(Uh, ferm, kappa, 2, norm, dirs)
     for sp, c in enumerate((1, 2, -1, 1j)):
         assert np.max(np.abs(both[..., sp, :] - c * one)) < 1e-12
+
+
+def test_program_operand_promotion():
+    """A colour vector v loads as the matrix [v 0 0] and a scalar s as s * 1, so
+    (U v)(x) of a program equals the matrix-vector product, and s * U scales."""
+    dims = (3, 2, 2, 3)
+    U = fieldgen.haar_su3(dims, 48)
+    v = fieldgen.color_vector(dims, 49)
+    s = np.random.default_rng(50).standard_normal(lattice.field_shape(dims)) + 0.5j
+    prog = [("loadl", 0, 0, 2, 1, -1), ("load", 1, 1, 1, -1), ("mul", 2, 0, 1), ("store", 2)]
+    got = expr.as_vector(expr.eval_program(prog, [U, v]))
+    ref = lattice.shift((U[..., 2, :, :] @ v[..., None])[..., 0], 1, -1)
+    assert np.max(np.abs(got - ref)) < 1e-14
+    prog = [("load", 0, 1, 0, 0), ("loadl", 1, 0, 3, 0, 0), ("mul", 2, 0, 1), ("store", 2)]
+    got = expr.eval_program(prog, [U, s])
+    assert np.max(np.abs(got - s[..., None, None] * U[..., 3, :, :])) < 1e-14
+    assert np.array_equal(expr.as_scalar(expr.as_matrix(s)), s)
