@@ -41,8 +41,22 @@ METRIC = "stout link-updates/s"
 # Cayley-Hamilton coefficients (+ FP64 re-projection in the FP32 path).
 BYTES_PER_LINK = {"f32": 144.0, "f64": 288.0}
 MATRIX_FLOPS_PER_LINK = 3019.0
-CH_FLOPS_PER_LINK = 214.0
 REPROJECT_FLOPS_PER_LINK = 142.0
+# Cayley-Hamilton coefficients: c0 = det Q and c1 = tr(Q^2)/2 (35 flops), then
+# either the closed form (179 more) or the reduced Taylor series of degree
+# 2K+1 by Horner's rule (14 per pair of terms: 14 (K-1) + 7).  K depends on
+# c1, so the average is counted on the workload itself (lq.stout_ch_stats).
+CH_PREAMBLE_FLOPS = 35.0
+CH_CLOSED_FORM_FLOPS = 214.0
+
+
+def ch_flops_per_link(stats):
+    """Average FP64 flops of the coefficient stage from (updates, series updates, sum of K)."""
+    n, n_series, sum_k = stats
+    if n == 0:
+        return CH_CLOSED_FORM_FLOPS
+    series = n_series * (CH_PREAMBLE_FLOPS + 7.0 - 14.0) + 14.0 * sum_k
+    return ((n - n_series) * CH_CLOSED_FORM_FLOPS + series) / n
 # GB300 unit counts: 152 SMs x 2 FP64 FMA lanes (304 per cycle) and x 128 FP32 FMA lanes.
 FP64_FMA_PER_CLK = 304
 FP32_FMA_PER_CLK = 152 * 128
@@ -53,10 +67,10 @@ TRAFFIC_BYTES_PER_LINK_F32 = (633602560 + 576611328) / 8388608.0
 TRAFFIC_BYTES_PER_LINK_F64 = (2051477760 + 1185383168) / 8388608.0
 
 
-def roofline(kernel_ms, links, prec, hbm_gbs, sm_mhz):
+def roofline(kernel_ms, links, prec, hbm_gbs, sm_mhz, ch_flops):
     """Roofline of one step-kernel launch: time bound of each resource from the
     algorithmic counts, the binding one reported as achieved / peak."""
-    f64_flops = CH_FLOPS_PER_LINK + (REPROJECT_FLOPS_PER_LINK if prec == "f32" else MATRIX_FLOPS_PER_LINK)
+    f64_flops = ch_flops + (REPROJECT_FLOPS_PER_LINK if prec == "f32" else MATRIX_FLOPS_PER_LINK)
     f32_flops = MATRIX_FLOPS_PER_LINK if prec == "f32" else 0.0
     p64 = 2.0 * FP64_FMA_PER_CLK * sm_mhz * 1e6
     p32 = 2.0 * FP32_FMA_PER_CLK * sm_mhz * 1e6
@@ -68,7 +82,7 @@ def roofline(kernel_ms, links, prec, hbm_gbs, sm_mhz):
     return {"bound": "alu", "pipe": "fp64", "achieved": ach64, "peak": p64 / 1e12, "unit": "TFLOP/s",
             "frac": ach64 / (p64 / 1e12), "traffic": traffic,
             "peak_source": f"derived: {FP64_FMA_PER_CLK} FP64 FMA/clk x 2 flops x {sm_mhz:.0f} MHz median SM clock",
-            "fp64_flops_per_link": f64_flops, "fp32_flops_per_link": f32_flops,
+            "fp64_flops_per_link": f64_flops, "ch_flops_per_link": ch_flops, "fp32_flops_per_link": f32_flops,
             "bytes_per_link": BYTES_PER_LINK[prec], "kernel_ms": kernel_ms,
             "t_bound_ms": {k: 1e3 * v for k, v in t.items()},
             "hbm_frac": BYTES_PER_LINK[prec] * links / sec / 1e9 / hbm_gbs}
@@ -301,6 +315,13 @@ def main():
     lq.stout_smear(f32, RHO, N_SMEAR, DIRS, **smear_opts)
     lq.stout_smear(f64, RHO, N_SMEAR, DIRS)
     p32, p64 = lq.plaquette(f32), lq.plaquette(f64)
+    # coefficient-stage work of this workload (series orders per link), for the flop count
+    f32.upload(U_host)
+    f64.upload(U_host)
+    ch32 = lq.stout_ch_stats(f32, RHO, N_SMEAR, DIRS)
+    ch64 = lq.stout_ch_stats(f64, RHO, N_SMEAR, DIRS)
+    lq.stout_smear(f32, RHO, N_SMEAR, DIRS, **smear_opts)
+    lq.stout_smear(f64, RHO, N_SMEAR, DIRS)
     d32 = f32.download()
     d64 = f64.download()
     err_32_64 = float(np.max(np.abs(d32.astype(np.complex128) - d64)))
@@ -347,15 +368,17 @@ def main():
         value64 = weak_scaling_value(links_per_step, world, step64 * 1e-3)
         links_per_launch = V * len(DIRS)
         mhz = clocks.get("sm_mhz") or 2070.0
-        roof32 = roofline(kern32, links_per_launch, "f32", hbm, mhz)
+        roof32 = roofline(kern32, links_per_launch, "f32", hbm, mhz, ch_flops_per_link(ch32))
+        roof32["ch_stats"] = {"link_updates": ch32[0], "series": ch32[1], "mean_K": ch32[2] / max(1, ch32[1])}
         tuned32 = lq.tune_lookup(lq.LQ_F32, DIMS, DIRS)
         var32 = args.variant or (tuned32[2] if tuned32 else 1)
-        roof32["kernel"] = "k_stout_smem<float,reproject>" if var32 == 2 else "k_stout_global<float,reproject>"
+        roof32["kernel"] = "k_stout_smem<float,reproject>" if var32 == 2 else "k_stout_global_f32<reproject>"
         roof32["launch"] = {"variant": var32, "tuned": tuned32}
         if var32 == 2:
             roof32["traffic"] = None   # DRAM counters of the shared-memory kernel not captured at this revision
-        roof64 = roofline(kern64, links_per_launch, "f64", hbm, mhz)
-        roof64["kernel"] = "k_stout_global<double>"
+        roof64 = roofline(kern64, links_per_launch, "f64", hbm, mhz, ch_flops_per_link(ch64))
+        roof64["ch_stats"] = {"link_updates": ch64[0], "series": ch64[1], "mean_K": ch64[2] / max(1, ch64[1])}
+        roof64["kernel"] = "k_stout_global_f64"
         roof64["launch"] = {"variant": 1, "tuned": lq.tune_lookup(lq.LQ_F64, DIMS, DIRS)}
         out = {
             "metric": METRIC, "value": value, "unit": "link-updates/s", "n_gpus": world, "steps": args.steps,

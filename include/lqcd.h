@@ -232,9 +232,24 @@ typedef struct lq_stout_opts {
  *   LQ_F32: staples, Omega, Q, exp assembly and U' = exp(iQ) U in FP32;
  *           Cayley-Hamilton coefficients f0,f1,f2 in FP64; SU(3)
  *           re-projection of every new link in FP64 (unless reproject = 0).
+ * The coefficients come from [MP] Sec. III's closed form, or, for
+ * c1 = tr(Q^2)/2 <= 3/4, from the Taylor series of exp(iQ) reduced with
+ * Q^3 = c1 Q + c0, truncated where its error bound is under 1e-17 (FP64
+ * links) or 1e-13 (FP32 links).
  * rho >= 0 and finite; n_steps >= 0; dirs_mask in [1, 15]. */
 lq_status lq_stout_smear(lq_field* links_inout, double rho, int n_steps, unsigned dirs_mask,
                          const lq_stout_opts* opts, void* stream);
+
+/* Coefficient-stage statistics of n_steps stout steps of `links` (which is
+ * not modified; the steps run on library scratch copies with the default
+ * launch shape and precision rules of lq_stout_smear).  counts[0] = link
+ * updates, counts[1] = updates whose Cayley-Hamilton coefficients took the
+ * truncated Taylor series (c1 <= 3/4), counts[2] = the sum of their series
+ * orders K (degree 2K+1).  The paper has no counterpart: this is
+ * instrumentation for counting the FP64 work of the coefficient stage, whose
+ * size depends on the field.  Synchronizes the stream. */
+lq_status lq_stout_ch_stats(const lq_field* links, double rho, int n_steps, unsigned dirs_mask,
+                            long long* counts, void* stream);
 
 typedef struct lq_backward_opts {
   int struct_size;        /* sizeof(lq_backward_opts); 0 => defaults                */
@@ -280,6 +295,15 @@ lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, in
  * scratch: s0 and one work copy of chi, allocated stream-ordered. */
 lq_status lq_jacobi_smear(const lq_field* links, lq_field* chi_inout, double kappa, int n_iter, double norm,
                           unsigned dirs_mask, void* stream);
+
+/* exp(iQ) of every matrix of a COLOR_MATRIX field of Hermitian traceless Q,
+ * through the same Cayley-Hamilton evaluation as the stout step ([MP]
+ * Sec. III): coefficients f0, f1, f2 in FP64 from c0 = det Q and
+ * c1 = tr(Q^2)/2, then f0 + f1 Q + f2 Q^2 in the field precision.  Only the
+ * Hermitian part of each input is read (upper triangle and real diagonal;
+ * the trace is removed in FP64).  out and q: same geometry and precision,
+ * distinct memory. */
+lq_status lq_expiq(lq_field* out, const lq_field* q, void* stream);
 
 /* Stout smearing that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot let a library

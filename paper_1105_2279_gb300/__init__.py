@@ -268,6 +268,20 @@ def stout_smear_noalloc(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
            "lq_stout_smear_noalloc")
 
 
+def stout_ch_stats(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
+    """(link updates, updates on the series branch, sum of series orders K) of
+    n_steps stout steps of `links` (lq_stout_ch_stats; links unchanged)."""
+    c = (c_longlong * 3)()
+    _check(L.load().lq_stout_ch_stats(links.handle, float(rho), int(n_steps), dirs_mask(dirs), c,
+                                      _stream(stream)), "lq_stout_ch_stats")
+    return int(c[0]), int(c[1]), int(c[2])
+
+
+def expiq(out, q, stream=None):
+    """out = exp(iQ) per site (Cayley-Hamilton, FP64 coefficients) of a COLOR_MATRIX field."""
+    _check(L.load().lq_expiq(out.handle, q.handle, _stream(stream)), "lq_expiq")
+
+
 def jacobi_smear(links, chi, kappa, n_iter, norm=1.0, dirs=(0, 1, 2, 3), stream=None):
     """In-place Jacobi smearing of a COLOR_VECTOR or FERMION field (Listing 1)."""
     _check(L.load().lq_jacobi_smear(links.handle, chi.handle, float(kappa), int(n_iter), float(norm),

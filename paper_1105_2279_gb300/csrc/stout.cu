@@ -22,10 +22,24 @@ struct MuList {
 // link by neighbouring staples).  Consecutive blocks take the smeared
 // directions of one site block, so the four sweeps share cached lines and
 // the field streams from DRAM about once per step.
-template <typename R, bool REPRO>
-__global__ void __launch_bounds__(256) k_stout_global(const typename vec2<R>::type* __restrict__ Uin,
-                                                      typename vec2<R>::type* __restrict__ Uout, GeomArgs g,
-                                                      R rho, unsigned dirs, int nsite, int nd, MuList ml) {
+// With COUNT, every warp adds to stats[0..2] its link updates, those whose
+// coefficients took the series, and the sum of their series orders K.
+__device__ __forceinline__ void count_series(unsigned long long* stats, int k) {
+  const unsigned m = __activemask();
+  const unsigned n_series = __reduce_add_sync(m, k > 0 ? 1u : 0u);
+  const unsigned sum_k = __reduce_add_sync(m, (unsigned)k);
+  if ((int)(threadIdx.x & 31) == __ffs(m) - 1) {
+    atomicAdd(&stats[0], (unsigned long long)__popc(m));
+    atomicAdd(&stats[1], (unsigned long long)n_series);
+    atomicAdd(&stats[2], (unsigned long long)sum_k);
+  }
+}
+
+template <typename R, bool REPRO, bool COUNT>
+__device__ __forceinline__ void stout_global_body(const typename vec2<R>::type* __restrict__ Uin,
+                                                  typename vec2<R>::type* __restrict__ Uout, const GeomArgs& g,
+                                                  R rho, unsigned dirs, int nsite, int nd, const MuList& ml,
+                                                  unsigned long long* stats) {
   const int mi = blockIdx.x % nd;
   const long long sb = blockIdx.x / nd;
   const int mu = mi == 0 ? ml.mu[0] : (mi == 1 ? ml.mu[1] : (mi == 2 ? ml.mu[2] : ml.mu[3]));
@@ -36,9 +50,29 @@ __global__ void __launch_bounds__(256) k_stout_global(const typename vec2<R>::ty
     const int s = (int)sl;
     int c[4];
     site_coords(g, s, c);
-    const M3<R> Up = stout_link<R>(Uin, g, s, c, mu, dirs, rho, REPRO);
+    int korder = 0;
+    const M3<R> Up = stout_link<R>(Uin, g, s, c, mu, dirs, rho, REPRO, COUNT ? &korder : nullptr);
     st_m3<R>(Uout + (long long)mu * 9 * V + s, V, Up);
+    if (COUNT) count_series(stats, korder);
   }
+}
+
+// FP32 links: capped at 72 registers (no spills), which fits 28 resident
+// warps per SM for blocks of 64 or 128 threads instead of 24: more warps to
+// keep the FP64 pipe, the step's bottleneck, fed.
+template <bool REPRO, bool COUNT = false>
+__global__ void __maxnreg__(72) k_stout_global_f32(const float2* __restrict__ Uin, float2* __restrict__ Uout,
+                                                   GeomArgs g, float rho, unsigned dirs, int nsite, int nd,
+                                                   MuList ml, unsigned long long* stats = nullptr) {
+  stout_global_body<float, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats);
+}
+
+template <bool REPRO, bool COUNT = false>
+__global__ void __launch_bounds__(256) k_stout_global_f64(const double2* __restrict__ Uin,
+                                                          double2* __restrict__ Uout, GeomArgs g, double rho,
+                                                          unsigned dirs, int nsite, int nd, MuList ml,
+                                                          unsigned long long* stats = nullptr) {
+  stout_global_body<double, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats);
 }
 
 // Variant 2 (FP32): shared-memory staging.  A CTA owns a BX x BY x BZ block of
@@ -191,14 +225,14 @@ static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int
   dim3 grid((unsigned)(((g.V + per_block - 1) / per_block) * nd));
   if (prec == LQ_F64) {
     if (reproject)
-      k_stout_global<double, true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml);
+      k_stout_global_f64<true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml);
     else
-      k_stout_global<double, false><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml);
+      k_stout_global_f64<false><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml);
   } else {
     if (reproject)
-      k_stout_global<float, true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd, ml);
+      k_stout_global_f32<true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd, ml);
     else
-      k_stout_global<float, false><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd, ml);
+      k_stout_global_f32<false><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd, ml);
   }
   return launch_check("stout step kernel");
 }
@@ -408,7 +442,65 @@ static lq_status run_graph(lq_field* f, double rho, int n, unsigned dirs, int re
 
 }  // namespace lq
 
+namespace lq {
+
+// exp(iQ) per site of a COLOR_MATRIX field (the stout step's exponential alone).
+template <typename R>
+__global__ void k_expiq(const typename vec2<R>::type* __restrict__ Q, typename vec2<R>::type* __restrict__ E,
+                        long long V) {
+  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const M3<R> m = ld_m3<R>(Q + sl, V);
+  QH<R> q;
+  q.d0 = m.e[0].re;
+  q.d1 = m.e[4].re;
+  q.d2 = m.e[8].re;
+  q.o01 = m.e[1];
+  q.o02 = m.e[2];
+  q.o12 = m.e[5];
+  const CHCoef f = ch_coefficients<sizeof(R) == 4 ? 1 : 2>(to_f64(q.d0), to_f64(q.d1), to_f64(q.d2),
+                                                           mkc(to_f64(q.o01.re), to_f64(q.o01.im)),
+                                                           mkc(to_f64(q.o02.re), to_f64(q.o02.im)),
+                                                           mkc(to_f64(q.o12.re), to_f64(q.o12.im)));
+  // the coefficients belong to the traceless part of Q: assemble with it
+  const R t = (q.d0 + q.d1 + q.d2) * R(1.0 / 3.0);
+  q.d0 -= t;
+  q.d1 -= t;
+  q.d2 -= t;
+  const M3<R> e = expiq_assemble(q, q_square(q), mkc<R>(from_f64<R>(f.f0.re), from_f64<R>(f.f0.im)),
+                                 mkc<R>(from_f64<R>(f.f1.re), from_f64<R>(f.f1.im)),
+                                 mkc<R>(from_f64<R>(f.f2.re), from_f64<R>(f.f2.im)));
+  st_m3<R>(E + sl, V, e);
+}
+
+}  // namespace lq
+
 using namespace lq;
+
+extern "C" lq_status lq_expiq(lq_field* out, const lq_field* q, void* stream) {
+  clear_error();
+  if (!out || !q) {
+    set_error("lq_expiq: NULL field");
+    return LQ_ERR_ARG;
+  }
+  if (out->kind != LQ_COLOR_MATRIX || q->kind != LQ_COLOR_MATRIX || out->prec != q->prec ||
+      !same_geom(out->geom, q->geom)) {
+    set_error("lq_expiq: out and q must be COLOR_MATRIX fields of one geometry and precision");
+    return LQ_ERR_GEOM;
+  }
+  if (out->ptr == q->ptr) {
+    set_error("lq_expiq: out must not alias q");
+    return LQ_ERR_ARG;
+  }
+  cudaStream_t s = as_stream(stream);
+  const long long V = q->geom.volume;
+  const unsigned grid = (unsigned)((V + 127) / 128);
+  if (q->prec == LQ_F64)
+    k_expiq<double><<<grid, 128, 0, s>>>((const double2*)q->ptr, (double2*)out->ptr, V);
+  else
+    k_expiq<float><<<grid, 128, 0, s>>>((const float2*)q->ptr, (float2*)out->ptr, V);
+  return launch_check("lq_expiq");
+}
 
 extern "C" lq_status lq_stout_smear(lq_field* links, double rho, int n_steps, unsigned dirs_mask,
                                     const lq_stout_opts* opts, void* stream) {
@@ -461,5 +553,59 @@ extern "C" lq_status lq_stout_smear(lq_field* links, double rho, int n_steps, un
   }
   st = stout_run_steps(links->ptr, work, links->geom, links->prec, rho, n_steps, dirs_mask, reproject, tc, s);
   if (own) scratch_free(work, s);
+  return st;
+}
+
+extern "C" lq_status lq_stout_ch_stats(const lq_field* links, double rho, int n_steps, unsigned dirs_mask,
+                                       long long* counts, void* stream) {
+  clear_error();
+  lq_status st = check_links(links, "lq_stout_ch_stats");
+  if (st != LQ_OK) return st;
+  if ((st = check_dirs(dirs_mask, "lq_stout_ch_stats")) != LQ_OK) return st;
+  if (!(rho >= 0.0) || rho > 1e6 || n_steps < 0 || !counts) {
+    set_error("lq_stout_ch_stats: need finite rho >= 0, n_steps >= 0 and a counts array");
+    return LQ_ERR_ARG;
+  }
+  for (int i = 0; i < 3; ++i) counts[i] = 0;
+  if (n_steps == 0) return LQ_OK;
+  cudaStream_t s = as_stream(stream);
+  void* buf[2] = {nullptr, nullptr};
+  void* dstats = nullptr;
+  for (int i = 0; i < 2 && st == LQ_OK; ++i) {
+    st = scratch_alloc(&buf[i], links->bytes, s, "lq_stout_ch_stats fields");
+    // links outside dirs are read by the staples and never written: both copies hold them
+    if (st == LQ_OK)
+      st = cuda_check(cudaMemcpyAsync(buf[i], links->ptr, links->bytes, cudaMemcpyDeviceToDevice, s),
+                      "lq_stout_ch_stats copy");
+  }
+  if (st == LQ_OK) st = scratch_alloc(&dstats, 3 * sizeof(unsigned long long), s, "lq_stout_ch_stats counters");
+  if (st == LQ_OK)
+    st = cuda_check(cudaMemsetAsync(dstats, 0, 3 * sizeof(unsigned long long), s), "lq_stout_ch_stats counters");
+  const GeomArgs g = geom_args(links->geom);
+  int nd = 0;
+  const MuList ml = mu_list(dirs_mask, &nd);
+  const int block = 128;
+  const dim3 grid((unsigned)(((g.V + block - 1) / block) * nd));
+  unsigned long long* ds = (unsigned long long*)dstats;
+  for (int k = 0; k < n_steps && st == LQ_OK; ++k) {
+    const void* in = buf[k % 2];
+    void* out = buf[(k + 1) % 2];
+    if (links->prec == LQ_F64)
+      k_stout_global_f64<false, true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho,
+                                                                 dirs_mask, 1, nd, ml, ds);
+    else
+      k_stout_global_f32<true, true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho,
+                                                               dirs_mask, 1, nd, ml, ds);
+    st = launch_check("lq_stout_ch_stats step");
+  }
+  unsigned long long h[3] = {0, 0, 0};
+  if (st == LQ_OK)
+    st = cuda_check(cudaMemcpyAsync(h, dstats, sizeof(h), cudaMemcpyDeviceToHost, s), "lq_stout_ch_stats read");
+  if (st == LQ_OK) st = cuda_check(cudaStreamSynchronize(s), "lq_stout_ch_stats sync");
+  for (int i = 0; i < 2; ++i)
+    if (buf[i]) scratch_free(buf[i], s);
+  if (dstats) scratch_free(dstats, s);
+  if (st == LQ_OK)
+    for (int i = 0; i < 3; ++i) counts[i] = (long long)h[i];
   return st;
 }

@@ -101,12 +101,151 @@ template <typename R> __device__ __forceinline__ QH<R> q_square(const QH<R>& q) 
 
 struct CHCoef {
   cx<double> f0, f1, f2;
+  int k;   // series order K (degree 2K+1) for small |Q|; 0 when the closed form was used
 };
+
+// ---- Small |Q|: the Taylor series of exp(iQ) reduced by Cayley-Hamilton ----
+// For traceless Hermitian Q, Q^3 = c1 Q + c0, so every power of Q, and any
+// polynomial in Q, is x + y Q + z Q^2.  exp(iQ) truncated at degree N is
+// evaluated by Horner's rule on that form: R <- R Q + a_n with
+// a_n = i^n / n! is (x, y, z) <- (c0 z + a_n, x + c1 z, y).  The truncation
+// error of the matrix series is at most rho^(N+1) / (N+1)! with
+// rho = |lambda|_max, and lambda_max^2 <= 4 c1 / 3 for a traceless 3x3
+// Hermitian matrix.  N = 2K+1 is the smallest odd degree whose bound is
+// under the tolerance: c1 <= (3/4) (tol (2K+2)!)^(1/(K+1)).  No term
+// cancels, unlike the closed form's h_j / (9u^2 - w^2) as Q -> 0.
+// kExpSeriesA[n] = i^n / n! without its factor i for odd n.
+static __constant__ double kExpSeriesA[24] = {
+    1.0, 1.0, -0.5, -0.16666666666666666, 0.041666666666666664, 0.008333333333333333,
+    -0.001388888888888889, -0.0001984126984126984, 2.48015873015873e-05, 2.7557319223985893e-06,
+    -2.755731922398589e-07, -2.505210838544172e-08, 2.08767569878681e-09, 1.6059043836821613e-10,
+    -1.1470745597729725e-11, -7.647163731819816e-13, 4.779477332387385e-14, 2.8114572543455206e-15,
+    -1.5619206968586225e-16, -8.22063524662433e-18, 4.110317623312165e-19, 1.9572941063391263e-20,
+    -8.896791392450574e-22, -3.868170170630684e-23};
+
+// IEEE-754 bit pattern of a positive normal double, at compile time; positive
+// doubles order like their bit patterns, so c1 is compared on the integer pipe.
+constexpr long long dbl_bits(double x) {
+  int e = 0;
+  while (x >= 2.0) { x *= 0.5; ++e; }
+  while (x < 1.0) { x *= 2.0; --e; }
+  return ((long long)(e + 1023) << 52) | (long long)((x - 1.0) * 4503599627370496.0);
+}
+
+// Largest c1 handled by the series (|lambda| <= 1); above it the closed form.
+#define LQ_SERIES_C1_MAX 0.75
+
+// Series order for c1: thresholds (3/4)(tol (2K+2)!)^(1/(K+1)) for K = 1..;
+// tol = 1e-13 on FP32 links (the f_j are rounded to FP32), 1e-17 on FP64.
+template <int NR> __device__ __forceinline__ int series_order(double c1) {
+  const long long b = __double_as_longlong(c1);
+  if (NR == 1) {
+    constexpr long long t[6] = {dbl_bits(1.161895e-06), dbl_bits(0.000312012573), dbl_bits(0.00597642391),
+                                dbl_bits(0.0386379317), dbl_bits(0.142928035), dbl_bits(0.380920096)};
+    int K = 1;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) K += (b > t[i]);
+    return K;   // <= 7: K = 7 covers c1 <= 0.8225
+  } else {
+    constexpr long long t[8] = {dbl_bits(1.161895e-08), dbl_bits(1.44823408e-05), dbl_bits(0.000597642391),
+                                dbl_bits(0.00612369949), dbl_bits(0.0307929118), dbl_bits(0.102189274),
+                                dbl_bits(0.260099018), dbl_bits(0.552627494)};
+    int K = 1;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) K += (b > t[i]);
+    return K;   // <= 9: K = 9 covers c1 <= 1.032
+  }
+}
+
+// f0 + f1 Q + f2 Q^2 = sum_{n <= 2K+1} (iQ)^n / n!  (c1 <= LQ_SERIES_C1_MAX).
+template <int KMAX>
+__device__ __forceinline__ void expiq_series(double c0, double c1, int K, CHCoef& f) {
+  const int N = 2 * K + 1;
+  // the three leading Horner steps from R = 0 give (a_{N-2}, a_{N-1}, a_N)
+  double xr = 0.0, xi = kExpSeriesA[N - 2];
+  double yr = kExpSeriesA[N - 1], yi = 0.0;
+  double zr = 0.0, zi = kExpSeriesA[N];
+#pragma unroll
+  for (int k = KMAX - 1; k >= 1; --k) {
+    if (k < K) {
+      // n = 2k (a_n real), then n = 2k - 1 (a_n imaginary)
+      double nxr = fma(zr, c0, kExpSeriesA[2 * k]), nxi = zi * c0;
+      double nyr = fma(zr, c1, xr), nyi = fma(zi, c1, xi);
+      zr = yr;
+      zi = yi;
+      xr = nxr;
+      xi = nxi;
+      yr = nyr;
+      yi = nyi;
+      nxr = zr * c0;
+      nxi = fma(zi, c0, kExpSeriesA[2 * k - 1]);
+      nyr = fma(zr, c1, xr);
+      nyi = fma(zi, c1, xi);
+      zr = yr;
+      zi = yi;
+      xr = nxr;
+      xi = nxi;
+      yr = nyr;
+      yi = nyi;
+    }
+  }
+  // n = 0
+  f.f0 = mkc(fma(zr, c0, 1.0), zi * c0);
+  f.f1 = mkc(fma(zr, c1, xr), fma(zi, c1, xi));
+  f.f2 = mkc(yr, yi);
+  f.k = K;
+}
+
+// f_j with b1_j = df_j/dc1 and b2_j = df_j/dc0 from the same series, by
+// differentiating each Horner step (forward mode):
+//   x' = c0 z + a_n,  dx'/dc0 = c0 dz/dc0 + z,  dx'/dc1 = c0 dz/dc1
+//   y' = x + c1 z,    dy'/dc0 = dx/dc0 + c1 dz/dc0,  dy'/dc1 = dx/dc1 + c1 dz/dc1 + z
+//   z' = y.
+// Without the series' cancellation-free form the closed-form b_ij lose
+// accuracy like 1e-16 / |Q|^4 as Q -> 0.  One more pair of terms than the
+// f_j alone keeps b_ij Q^j at FP64 rounding for all c1 <= 3/4.
+template <int KMAX>
+__device__ __forceinline__ void expiq_series_deriv(double c0, double c1, int K, cx<double> f[3],
+                                                   cx<double> b1[3], cx<double> b2[3]) {
+  cx<double> x = mkc(0.0, 0.0), y = x, z = x, x0 = x, y0 = x, z0 = x, x1 = x, y1 = x, z1 = x;
+#pragma unroll
+  for (int n = 2 * KMAX + 1; n >= 0; --n) {
+    if (n <= 2 * K + 1) {
+      const cx<double> a = (n & 1) ? mkc(0.0, kExpSeriesA[n]) : mkc(kExpSeriesA[n], 0.0);
+      const cx<double> nx = mkc(fma(z.re, c0, a.re), fma(z.im, c0, a.im));
+      const cx<double> nx0 = mkc(fma(z0.re, c0, z.re), fma(z0.im, c0, z.im));
+      const cx<double> nx1 = mkc(z1.re * c0, z1.im * c0);
+      const cx<double> ny = mkc(fma(z.re, c1, x.re), fma(z.im, c1, x.im));
+      const cx<double> ny0 = mkc(fma(z0.re, c1, x0.re), fma(z0.im, c1, x0.im));
+      const cx<double> ny1 = mkc(fma(z1.re, c1, x1.re + z.re), fma(z1.im, c1, x1.im + z.im));
+      z = y;
+      z0 = y0;
+      z1 = y1;
+      x = nx;
+      x0 = nx0;
+      x1 = nx1;
+      y = ny;
+      y0 = ny0;
+      y1 = ny1;
+    }
+  }
+  f[0] = x;
+  f[1] = y;
+  f[2] = z;
+  b1[0] = x1;
+  b1[1] = y1;
+  b1[2] = z1;
+  b2[0] = x0;
+  b2[1] = y0;
+  b2[2] = z0;
+}
 
 // Cayley-Hamilton coefficients of exp(iQ) = f0 + f1 Q + f2 Q^2, in FP64
 // (Morningstar & Peardon 2004, Sec. III).  The input Q is re-made exactly
-// traceless in FP64 first.  The same quantities as the paper's formulas are
-// formed with few FP64 instructions (fp64_math.cuh):
+// traceless in FP64 first.  For c1 <= 3/4 (all |lambda| <= 1, every link of
+// a smearing run on fields with plaquette >~ 0.5) the reduced Taylor series
+// above; otherwise the paper's closed form, its quantities formed with few
+// FP64 instructions (fp64_math.cuh):
 //   1/sqrt(c1/3) by Newton;  |c0|/c0max = |c0| (1/sqrt(c1/3))^3 / 2;
 //   cos(theta/3) as the root of 4y^3 - 3y = |c0|/c0max;  w^2 = c1 (1 - y^2);
 //   cos w and xi0(w) = sin(w)/w from w^2 by their series when w <= pi/4.
@@ -124,7 +263,12 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
   const cx<double> p = cmul(o01, o12);
   const double re3 = p.re * o02.re + p.im * o02.im;
   const double c0 = d0 * d1 * d2 - d0 * n12 - d1 * n02 - d2 * n01 + 2.0 * re3;
-  if (!(c1 >= LQ_C1_SERIES)) {  // also catches NaN
+  if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {  // c1 >= +0: integer compare
+    expiq_series<NR == 1 ? 7 : 9>(c0, c1, series_order<NR>(c1), f);
+    return f;
+  }
+  f.k = 0;
+  if (!(c1 >= LQ_C1_SERIES)) {  // NaN (small c1 took the series)
     f.f0 = mkc(1.0, 0.0);
     f.f1 = mkc(0.0, 1.0);
     f.f2 = mkc(-0.5, 0.0);
@@ -172,7 +316,8 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
 }
 
 // f_j and their derivatives b1_j = df_j/dc1, b2_j = df_j/dc0 (FP64), for the
-// stout force (Morningstar & Peardon 2004, Sec. IV).  With c1 = 3u^2 + w^2,
+// stout force (Morningstar & Peardon 2004, Sec. IV).  For c1 <= 3/4 from the
+// differentiated series (expiq_series_deriv); otherwise the closed form:  With c1 = 3u^2 + w^2,
 // c0 = 2u(u^2 - w^2) and D = 9u^2 - w^2 the chain rule through (u, w) gives
 //   b1_j = [2u r1_j + (3u^2 - w^2) r2_j - 2(15u^2 + w^2) f_j] / (2 D^2)
 //   b2_j = [r1_j - 3u r2_j - 24u f_j] / (2 D^2)
@@ -193,7 +338,11 @@ __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, d
   const cx<double> p = cmul(o01, o12);
   const double re3 = p.re * o02.re + p.im * o02.im;
   const double c0 = d0 * d1 * d2 - d0 * n12 - d1 * n02 - d2 * n01 + 2.0 * re3;
-  if (!(c1 >= LQ_C1_SERIES)) {
+  if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {
+    expiq_series_deriv<10>(c0, c1, series_order<2>(c1) + 1, r.f, r.b1, r.b2);
+    return r;
+  }
+  if (!(c1 >= LQ_C1_SERIES)) {  // NaN (small c1 took the series)
     // Q -> 0: exp(iQ) = 1 + iQ - Q^2/2 - iQ^3/6 + Q^4/24 + iQ^5/120 ... reduced
     // with Q^3 = c1 Q + c0 gives these first derivatives at Q = 0.
     r.f[0] = mkc(1.0, 0.0);
@@ -360,7 +509,8 @@ template <typename R> __device__ __forceinline__ M3<R> reproject_via_f64(const M
 // New link from the bare staple sum S and U_mu(x): FP64 coefficients always;
 // matrix algebra in R; optional FP64 re-projection.
 template <typename R>
-__device__ __forceinline__ M3<R> stout_update(const M3<R>& S, const M3<R>& Umu, R rho, bool reproject) {
+__device__ __forceinline__ M3<R> stout_update(const M3<R>& S, const M3<R>& Umu, R rho, bool reproject,
+                                              int* korder = nullptr) {
   // Q is linear in Omega = rho S U^dag: scale the 9 real components of Q
   // instead of the 18 of the staple sum
   const QH<R> q = q_rscale(q_from_omega(mul_nd(S, Umu)), rho);
@@ -374,6 +524,7 @@ __device__ __forceinline__ M3<R> stout_update(const M3<R>& S, const M3<R>& Umu, 
                                  mkc<R>(from_f64<R>(f.f2.re), from_f64<R>(f.f2.im)));
   M3<R> Up = mul_nn(E, Umu);
   if (reproject) Up = reproject_via_f64(Up);
+  if (korder) *korder = f.k;
   return Up;
 }
 
@@ -381,8 +532,9 @@ __device__ __forceinline__ M3<R> stout_update(const M3<R>& S, const M3<R>& Umu, 
 template <typename R>
 __device__ __forceinline__ M3<R> stout_link(const typename vec2<R>::type* __restrict__ U,
                                             const GeomArgs& g, int s, const int c[4], int mu,
-                                            unsigned dirs, R rho, bool reproject) {
-  return stout_update<R>(staple_sum<R>(U, g, s, c, mu, dirs), ld_link<R>(U, g.V, mu, s), rho, reproject);
+                                            unsigned dirs, R rho, bool reproject, int* korder = nullptr) {
+  return stout_update<R>(staple_sum<R>(U, g, s, c, mu, dirs), ld_link<R>(U, g.V, mu, s), rho, reproject,
+                         korder);
 }
 
 }  // namespace lq

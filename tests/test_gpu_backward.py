@@ -54,6 +54,19 @@ def test_force_with_given_seed(gpu):
     assert np.max(np.abs(G - G_ref)) <= 1e-11 * np.max(np.abs(G_ref))
 
 
+@pytest.mark.parametrize("eps", [0.02, 0.002])
+def test_force_smooth_fields(gpu, eps):
+    """Fields near the identity give |Q| ~ 6 rho eps, where the closed-form
+    derivative coefficients of MP Sec. IV lose accuracy like 1e-16/|Q|^4
+    (2e-9 relative at |Q| = 0.01); the gradient must stay at FP64 rounding."""
+    dims = (3, 4, 3, 4)
+    U = fieldgen.near_identity_su3(dims, 304, eps=eps)
+    seed = fieldgen.haar_su3(dims, 305) * 0.7
+    G_ref = backward.stout_backward(U, 0.1, 2, ALL, seed)
+    _, G = gpu_force(U, lq.LQ_F64, 0.1, 2, ALL, seed=seed)
+    assert np.max(np.abs(G - G_ref)) <= 1e-12 * np.max(np.abs(G_ref))
+
+
 @pytest.mark.parametrize("n,dirs", [(1, ALL), (2, SPATIAL)])
 def test_force_f32(gpu, n, dirs):
     dims = (4, 3, 4, 3)

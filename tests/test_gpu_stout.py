@@ -36,6 +36,7 @@ def _run(U, prec, rho, n, dirs, **opts):
     ((5, 3, 2, 7), "haar", 0.25, 2, (1, 3)),
     ((6, 6, 6, 12), "near", 0.1, 4, ALL),
     ((8, 8, 8, 16), "near", 0.1, 2, SPATIAL),
+    ((4, 4, 4, 4), "haar", 0.4, 2, ALL),          # ~40 % of links past the series domain c1 <= 3/4
 ])
 def test_f64_matches_oracle(gpu, dims, gen, rho, n, dirs):
     U = fieldgen.haar_su3(dims, 100) if gen == "haar" else fieldgen.near_identity_su3(dims, 100)
@@ -53,6 +54,7 @@ def test_f64_matches_oracle(gpu, dims, gen, rho, n, dirs):
     ((3, 4, 5, 6), "near", 0.125, 3, ALL),
     ((6, 5, 4, 8), "near", 0.1, 6, SPATIAL),
     ((2, 2, 2, 2), "haar", 0.1, 2, ALL),
+    ((4, 4, 4, 4), "haar", 0.4, 2, ALL),
 ])
 def test_f32_mixed_matches_oracle(gpu, dims, gen, rho, n, dirs):
     U = fieldgen.haar_su3(dims, 101) if gen == "haar" else fieldgen.near_identity_su3(dims, 101)
