@@ -240,6 +240,25 @@ typedef struct lq_stout_opts {
 lq_status lq_stout_smear(lq_field* links_inout, double rho, int n_steps, unsigned dirs_mask,
                          const lq_stout_opts* opts, void* stream);
 
+/* Stout smearing of links in HOST memory, end to end, with the transfers
+ * overlapped with the arithmetic.  host_in / host_out: the AoS link layout
+ * of lq_field_upload / lq_field_download for `geom` and `prec` (host_out
+ * may equal host_in; page-locked memory lets the copies run asynchronously).
+ * The lattice is cut into n_chunks slabs of whole t-slices (0: 8, at most
+ * dims[3]); each slab is copied and transposed to the device layout as it
+ * arrives, the first step of a slab starts once it and its two neighbouring
+ * slabs are resident, and each slab of the final field is transposed back
+ * and copied out as soon as its last step is done.  Arithmetic, rules and
+ * results are those of lq_stout_smear (bit for bit, global-load kernel; the
+ * launch shape comes from opts->block, else a cached tuning result, else the
+ * default).  plaq_out (optional, 3 doubles) receives lq_plaquette of the
+ * result.  Device memory: three link fields from the library pool.
+ * Synchronizes the stream.  ([W] Sec. 4.3 moves fields between host and
+ * device on demand; here the transfers run behind the smearing.) */
+lq_status lq_stout_smear_host(const void* host_in, void* host_out, const lq_geom* geom, int prec, double rho,
+                              int n_steps, unsigned dirs_mask, int n_chunks, double* plaq_out,
+                              const lq_stout_opts* opts, void* stream);
+
 /* Coefficient-stage statistics of n_steps stout steps of `links` (which is
  * not modified; the steps run on library scratch copies with the default
  * launch shape and precision rules of lq_stout_smear).  counts[0] = link

@@ -42,6 +42,8 @@ def _check(st, what):
 
 def _stream(stream):
     if stream is not None:
+        if hasattr(stream, "cuda_stream"):      # torch.cuda.Stream
+            return c_void_p(stream.cuda_stream)
         return c_void_p(int(stream))
     import torch
     return c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -266,6 +268,39 @@ def stout_smear_noalloc(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
     """lq_stout_smear_noalloc: same result as stout_smear, no device allocation (fields up to 32 MiB)."""
     _check(L.load().lq_stout_smear_noalloc(links.handle, float(rho), int(n_steps), dirs_mask(dirs), _stream(stream)),
            "lq_stout_smear_noalloc")
+
+
+def _host_ptr(a):
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):       # torch tensor (e.g. page-locked)
+        return int(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host array must be C-contiguous")
+        return int(a.ctypes.data)
+    raise TypeError(f"cannot take a host pointer from {type(a).__name__}")
+
+
+def stout_smear_host(host_in, host_out, geom, prec, rho, n_steps, dirs=(0, 1, 2, 3), n_chunks=0, stream=None,
+                     **opts):
+    """lq_stout_smear_host: AoS links in host memory -> smeared AoS links in host memory, the
+    transfers overlapped with the smearing; returns lq_plaquette of the result.  host_in/out:
+    numpy arrays, torch tensors (page-locked for asynchronous copies) or raw pointers."""
+    g = geom if isinstance(geom, Geometry) else Geometry(geom)
+    for a in (host_in, host_out):
+        nb = getattr(a, "nbytes", None)
+        if nb is None and hasattr(a, "element_size"):
+            nb = a.element_size() * a.numel()
+        need = g.volume * 36 * (8 if prec == LQ_F32 else 16)
+        if nb is not None and nb != need:
+            raise ValueError(f"host buffer has {nb} bytes, the links need {need}")
+    o = stout_opts(**opts)
+    out = (c_double * 3)()
+    _check(L.load().lq_stout_smear_host(c_void_p(_host_ptr(host_in)), c_void_p(_host_ptr(host_out)), g.handle,
+                                        int(prec), float(rho), int(n_steps), dirs_mask(dirs), int(n_chunks), out,
+                                        byref(o), _stream(stream)), "lq_stout_smear_host")
+    return out[0], out[1], out[2]
 
 
 def stout_ch_stats(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):

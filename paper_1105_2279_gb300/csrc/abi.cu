@@ -166,12 +166,12 @@ constexpr int kTileThreads = 256;
 
 template <typename E>
 __global__ void __launch_bounds__(kTileThreads) aos_to_soa(const E* __restrict__ aos, E* __restrict__ soa, long long V,
-                                                           int per_site) {
+                                                           int per_site, long long s_begin, long long s_end) {
   extern __shared__ __align__(16) unsigned char tile_raw[];
   E* tile = reinterpret_cast<E*>(tile_raw);  // [kTileSites][per_site + 1]
   const int ld = per_site + 1;
-  const long long s0 = (long long)blockIdx.x * kTileSites;
-  const int ns = (int)min((long long)kTileSites, V - s0);
+  const long long s0 = s_begin + (long long)blockIdx.x * kTileSites;
+  const int ns = (int)min((long long)kTileSites, s_end - s0);
   const int n = ns * per_site;
   const E* src = aos + s0 * per_site;
   for (int i = threadIdx.x; i < n; i += kTileThreads) {
@@ -186,12 +186,12 @@ __global__ void __launch_bounds__(kTileThreads) aos_to_soa(const E* __restrict__
 }
 template <typename E>
 __global__ void __launch_bounds__(kTileThreads) soa_to_aos(const E* __restrict__ soa, E* __restrict__ aos, long long V,
-                                                           int per_site) {
+                                                           int per_site, long long s_begin, long long s_end) {
   extern __shared__ __align__(16) unsigned char tile_raw[];
   E* tile = reinterpret_cast<E*>(tile_raw);
   const int ld = per_site + 1;
-  const long long s0 = (long long)blockIdx.x * kTileSites;
-  const int ns = (int)min((long long)kTileSites, V - s0);
+  const long long s0 = s_begin + (long long)blockIdx.x * kTileSites;
+  const int ns = (int)min((long long)kTileSites, s_end - s0);
   const int n = ns * per_site;
   for (int i = threadIdx.x; i < n; i += kTileThreads) {
     const int c = i / ns, j = i - c * ns;
@@ -205,17 +205,19 @@ __global__ void __launch_bounds__(kTileThreads) soa_to_aos(const E* __restrict__
   }
 }
 
-static lq_status transpose(const void* src, void* dst, const lq_field* f, bool to_soa, cudaStream_t s) {
-  const long long V = f->geom.volume;
-  const int per_site = ndir_of(f->kind) * ncomp_of(f->kind);
-  const size_t eb = elem_bytes(f->kind, f->prec);
-  const unsigned blocks = (unsigned)((V + kTileSites - 1) / kTileSites);
+lq_status transpose_range(const void* src, void* dst, const lq_geom& g, int kind, int prec, bool to_soa,
+                          long long s_begin, long long s_end, cudaStream_t s) {
+  const long long V = g.volume;
+  const int per_site = ndir_of(kind) * ncomp_of(kind);
+  const size_t eb = elem_bytes(kind, prec);
+  const unsigned blocks = (unsigned)((s_end - s_begin + kTileSites - 1) / kTileSites);
+  if (blocks == 0) return LQ_OK;
   const size_t smem = (size_t)kTileSites * (per_site + 1) * eb;  // <= 64 * 37 * 16 B = 37.9 KB
-#define LQ_T(E)                                                                                     \
-  if (to_soa)                                                                                       \
-    aos_to_soa<E><<<blocks, kTileThreads, smem, s>>>((const E*)src, (E*)dst, V, per_site);         \
-  else                                                                                              \
-    soa_to_aos<E><<<blocks, kTileThreads, smem, s>>>((const E*)src, (E*)dst, V, per_site);
+#define LQ_T(E)                                                                                            \
+  if (to_soa)                                                                                              \
+    aos_to_soa<E><<<blocks, kTileThreads, smem, s>>>((const E*)src, (E*)dst, V, per_site, s_begin, s_end);  \
+  else                                                                                                     \
+    soa_to_aos<E><<<blocks, kTileThreads, smem, s>>>((const E*)src, (E*)dst, V, per_site, s_begin, s_end);
   if (eb == 4) {
     LQ_T(float)
   } else if (eb == 8) {
@@ -225,6 +227,10 @@ static lq_status transpose(const void* src, void* dst, const lq_field* f, bool t
   }
 #undef LQ_T
   return launch_check(to_soa ? "aos_to_soa" : "soa_to_aos");
+}
+
+static lq_status transpose(const void* src, void* dst, const lq_field* f, bool to_soa, cudaStream_t s) {
+  return transpose_range(src, dst, f->geom, f->kind, f->prec, to_soa, 0, f->geom.volume, s);
 }
 
 }  // namespace lq

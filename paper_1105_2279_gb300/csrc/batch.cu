@@ -29,11 +29,11 @@ struct MuList4 {
 };
 
 template <typename R, bool REPRO>
-__global__ void __launch_bounds__(256) k_stout_batch(const BatchDesc* __restrict__ D, int n_cfg, long long n_items,
-                                                     unsigned long long* __restrict__ counter, int parity, R rho,
-                                                     unsigned dirs, int nsite, int nd, MuList4 ml) {
+__device__ __forceinline__ void stout_batch_body(const BatchDesc* __restrict__ D, int n_cfg, long long n_items,
+                                                 unsigned long long* __restrict__ counter, int parity, R rho,
+                                                 unsigned dirs, int nsite, int nd, const MuList4& ml,
+                                                 long long& item_s) {
   typedef typename vec2<R>::type V2;
-  __shared__ long long item_s;
   for (;;) {
     if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ULL);
     __syncthreads();
@@ -66,6 +66,25 @@ __global__ void __launch_bounds__(256) k_stout_batch(const BatchDesc* __restrict
       st_m3<R>(out + (long long)mu * 9 * V + s, V, Up);
     }
   }
+}
+
+// FP32 links: capped at 80 registers (24 resident warps per SM instead of 16;
+// ptxas reports 24 bytes of spill stores per thread).
+template <bool REPRO>
+__global__ void __maxnreg__(80) k_stout_batch_f32(const BatchDesc* __restrict__ D, int n_cfg, long long n_items,
+                                                  unsigned long long* __restrict__ counter, int parity, float rho,
+                                                  unsigned dirs, int nsite, int nd, MuList4 ml) {
+  __shared__ long long item_s;
+  stout_batch_body<float, REPRO>(D, n_cfg, n_items, counter, parity, rho, dirs, nsite, nd, ml, item_s);
+}
+
+template <bool REPRO>
+__global__ void __launch_bounds__(256) k_stout_batch_f64(const BatchDesc* __restrict__ D, int n_cfg,
+                                                         long long n_items, unsigned long long* __restrict__ counter,
+                                                         int parity, double rho, unsigned dirs, int nsite, int nd,
+                                                         MuList4 ml) {
+  __shared__ long long item_s;
+  stout_batch_body<double, REPRO>(D, n_cfg, n_items, counter, parity, rho, dirs, nsite, nd, ml, item_s);
 }
 
 struct BatchPlan {
@@ -140,14 +159,14 @@ static lq_status batch_sequence(lq_field* const* links, int n_cfg, const BatchPl
     unsigned long long* ctr = p.counters + k;
     if (prec == LQ_F64) {
       if (reproject)
-        k_stout_batch<double, true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, nd, ml);
+        k_stout_batch_f64<true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, nd, ml);
       else
-        k_stout_batch<double, false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, nd, ml);
+        k_stout_batch_f64<false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, rho, dirs, tc.nsite, nd, ml);
     } else {
       if (reproject)
-        k_stout_batch<float, true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, nd, ml);
+        k_stout_batch_f32<true><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, nd, ml);
       else
-        k_stout_batch<float, false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, nd, ml);
+        k_stout_batch_f32<false><<<grid, tc.block, 0, s>>>(p.dev, n_cfg, p.n_items, ctr, parity, (float)rho, dirs, tc.nsite, nd, ml);
     }
     if ((st = launch_check("k_stout_batch"))) return st;
   }

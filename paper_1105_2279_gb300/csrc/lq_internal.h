@@ -99,6 +99,14 @@ lq_status stout_run_steps(void* links, void* work, const lq_geom& g, int prec, d
                           int n_steps, unsigned dirs, int reproject, const TuneChoice& tc,
                           cudaStream_t s);
 TuneChoice stout_default_choice(int prec);
+// One stout step over the sites [s_begin, s_end) only (global-load kernel).
+lq_status stout_step_range(const void* in, void* out, const lq_geom& g, int prec, double rho, unsigned dirs,
+                           int reproject, const TuneChoice& tc, long long s_begin, long long s_end,
+                           cudaStream_t s);
+// AoS <-> SoA transpose of the sites [s_begin, s_end) of a field of this kind,
+// between a whole-lattice AoS buffer and a whole-lattice SoA buffer.
+lq_status transpose_range(const void* src, void* dst, const lq_geom& g, int kind, int prec, bool to_soa,
+                          long long s_begin, long long s_end, cudaStream_t s);
 lq_status stout_choose(const lq_field* f, double rho, unsigned dirs, int reproject,
                        const lq_stout_opts* o, cudaStream_t s, TuneChoice* out);
 

@@ -35,18 +35,20 @@ __device__ __forceinline__ void count_series(unsigned long long* stats, int k) {
   }
 }
 
+// Sites [s_begin, s_end) of the lattice (the whole lattice, or one slab of
+// t-slices when the host-streamed path smears slab by slab).
 template <typename R, bool REPRO, bool COUNT>
 __device__ __forceinline__ void stout_global_body(const typename vec2<R>::type* __restrict__ Uin,
                                                   typename vec2<R>::type* __restrict__ Uout, const GeomArgs& g,
                                                   R rho, unsigned dirs, int nsite, int nd, const MuList& ml,
-                                                  unsigned long long* stats) {
+                                                  unsigned long long* stats, int s_begin, int s_end) {
   const int mi = blockIdx.x % nd;
   const long long sb = blockIdx.x / nd;
   const int mu = mi == 0 ? ml.mu[0] : (mi == 1 ? ml.mu[1] : (mi == 2 ? ml.mu[2] : ml.mu[3]));
   const long long V = g.V;
   for (int k = 0; k < nsite; ++k) {
-    const long long sl = (sb * nsite + k) * blockDim.x + threadIdx.x;
-    if (sl >= V) return;
+    const long long sl = s_begin + (sb * nsite + k) * blockDim.x + threadIdx.x;
+    if (sl >= s_end) return;
     const int s = (int)sl;
     int c[4];
     site_coords(g, s, c);
@@ -63,16 +65,16 @@ __device__ __forceinline__ void stout_global_body(const typename vec2<R>::type* 
 template <bool REPRO, bool COUNT = false>
 __global__ void __maxnreg__(72) k_stout_global_f32(const float2* __restrict__ Uin, float2* __restrict__ Uout,
                                                    GeomArgs g, float rho, unsigned dirs, int nsite, int nd,
-                                                   MuList ml, unsigned long long* stats = nullptr) {
-  stout_global_body<float, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats);
+                                                   MuList ml, unsigned long long* stats, int s_begin, int s_end) {
+  stout_global_body<float, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats, s_begin, s_end);
 }
 
 template <bool REPRO, bool COUNT = false>
 __global__ void __launch_bounds__(256) k_stout_global_f64(const double2* __restrict__ Uin,
                                                           double2* __restrict__ Uout, GeomArgs g, double rho,
                                                           unsigned dirs, int nsite, int nd, MuList ml,
-                                                          unsigned long long* stats = nullptr) {
-  stout_global_body<double, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats);
+                                                          unsigned long long* stats, int s_begin, int s_end) {
+  stout_global_body<double, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats, s_begin, s_end);
 }
 
 // Variant 2 (FP32): shared-memory staging.  A CTA owns a BX x BY x BZ block of
@@ -191,6 +193,43 @@ static MuList mu_list(unsigned dirs, int* n) {
   return m;
 }
 
+// One step on the global-load kernel over sites [s_begin, s_end).
+static lq_status launch_global(const void* in, void* out, const GeomArgs& g, int prec, double rho, unsigned dirs,
+                               int reproject, const TuneChoice& tc, long long s_begin, long long s_end,
+                               cudaStream_t s) {
+  int nd = 0;
+  const MuList ml = mu_list(dirs, &nd);
+  const int block = tc.block > 0 ? tc.block : 128;
+  const int nsite = tc.nsite > 0 ? tc.nsite : 1;
+  const long long per_block = (long long)block * nsite;
+  const int sb = (int)s_begin, se = (int)s_end;
+  dim3 grid((unsigned)(((s_end - s_begin + per_block - 1) / per_block) * nd));
+  if (grid.x == 0) return LQ_OK;
+  if (prec == LQ_F64) {
+    if (reproject)
+      k_stout_global_f64<true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml,
+                                                      nullptr, sb, se);
+    else
+      k_stout_global_f64<false><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd,
+                                                       ml, nullptr, sb, se);
+  } else {
+    if (reproject)
+      k_stout_global_f32<true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd,
+                                                      ml, nullptr, sb, se);
+    else
+      k_stout_global_f32<false><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite,
+                                                       nd, ml, nullptr, sb, se);
+  }
+  return launch_check("stout step kernel");
+}
+
+lq_status stout_step_range(const void* in, void* out, const lq_geom& geom, int prec, double rho, unsigned dirs,
+                           int reproject, const TuneChoice& tc, long long s_begin, long long s_end, cudaStream_t s) {
+  TuneChoice t = tc;
+  if (t.variant == 2) t = stout_default_choice(prec);   // the shared-memory variant tiles whole lattices
+  return launch_global(in, out, geom_args(geom), prec, rho, dirs, reproject, t, s_begin, s_end, s);
+}
+
 static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int prec, double rho,
                              unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s) {
   const GeomArgs g = geom_args(geom);
@@ -219,22 +258,7 @@ static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int
           (const float2*)in, (float2*)out, g, (float)rho, dirs, nd, ml, tchunk);
     return launch_check("stout step kernel (shared-memory variant)");
   }
-  const int block = tc.block > 0 ? tc.block : 128;
-  const int nsite = tc.nsite > 0 ? tc.nsite : 1;
-  const long long per_block = (long long)block * nsite;
-  dim3 grid((unsigned)(((g.V + per_block - 1) / per_block) * nd));
-  if (prec == LQ_F64) {
-    if (reproject)
-      k_stout_global_f64<true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml);
-    else
-      k_stout_global_f64<false><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho, dirs, nsite, nd, ml);
-  } else {
-    if (reproject)
-      k_stout_global_f32<true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd, ml);
-    else
-      k_stout_global_f32<false><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho, dirs, nsite, nd, ml);
-  }
-  return launch_check("stout step kernel");
+  return launch_global(in, out, g, prec, rho, dirs, reproject, tc, 0, g.V, s);
 }
 
 static size_t dir_block_bytes(const lq_geom& g, int prec) {
@@ -592,10 +616,10 @@ extern "C" lq_status lq_stout_ch_stats(const lq_field* links, double rho, int n_
     void* out = buf[(k + 1) % 2];
     if (links->prec == LQ_F64)
       k_stout_global_f64<false, true><<<grid, block, 0, s>>>((const double2*)in, (double2*)out, g, rho,
-                                                                 dirs_mask, 1, nd, ml, ds);
+                                                                 dirs_mask, 1, nd, ml, ds, 0, g.V);
     else
       k_stout_global_f32<true, true><<<grid, block, 0, s>>>((const float2*)in, (float2*)out, g, (float)rho,
-                                                               dirs_mask, 1, nd, ml, ds);
+                                                               dirs_mask, 1, nd, ml, ds, 0, g.V);
     st = launch_check("lq_stout_ch_stats step");
   }
   unsigned long long h[3] = {0, 0, 0};

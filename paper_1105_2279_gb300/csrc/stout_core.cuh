@@ -26,12 +26,17 @@ __device__ __forceinline__ M3<R> staple_sum(const typename vec2<R>::type* __rest
   M3<R> C;
   m_zero(C);
   const int s_pmu = nb_fwd(g, s, coord_of(c, mu), mu);
-#pragma unroll
+  // not unrolled: one copy of the six products keeps the kernel's hot code
+  // small (instruction-fetch stalls dominated the unrolled form)
+#pragma unroll 1
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu || !((dirs >> nu) & 1u)) continue;
-    const int s_pnu = nb_fwd(g, s, c[nu], nu);
-    const int s_mnu = nb_bwd(g, s, c[nu], nu);
-    const int s_pmu_mnu = nb_bwd(g, s_pmu, c[nu], nu);
+    const int cn = coord_of(c, nu);
+    const int Ln = nu == 0 ? g.L[0] : (nu == 1 ? g.L[1] : (nu == 2 ? g.L[2] : g.L[3]));
+    const int sn = nu == 0 ? g.stride[0] : (nu == 1 ? g.stride[1] : (nu == 2 ? g.stride[2] : g.stride[3]));
+    const int s_pnu = (cn + 1 < Ln) ? s + sn : s - (Ln - 1) * sn;
+    const int s_mnu = (cn > 0) ? s - sn : s + (Ln - 1) * sn;
+    const int s_pmu_mnu = (cn > 0) ? s_pmu - sn : s_pmu + (Ln - 1) * sn;
     {
       M3<R> t = mul_nd(ld_link<R>(U, V, mu, s_pnu), ld_link<R>(U, V, nu, s_pmu));
       mac_nn(C, ld_link<R>(U, V, nu, s), t);
