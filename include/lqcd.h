@@ -244,7 +244,7 @@ lq_status lq_stout_smear(lq_field* links_inout, double rho, int n_steps, unsigne
  * overlapped with the arithmetic.  host_in / host_out: the AoS link layout
  * of lq_field_upload / lq_field_download for `geom` and `prec` (host_out
  * may equal host_in; page-locked memory lets the copies run asynchronously).
- * The lattice is cut into n_chunks slabs of whole t-slices (0: 8, at most
+ * The lattice is cut into n_chunks slabs of whole t-slices (0: 16, at most
  * dims[3]); each slab is copied and transposed to the device layout as it
  * arrives, the first step of a slab starts once it and its two neighbouring
  * slabs are resident, and each slab of the final field is transposed back

@@ -5,17 +5,25 @@
 //   upload stream:   per slab, H2D copy into an AoS staging buffer, then the
 //                    AoS -> SoA transpose of that slab; event up[i].
 //   compute stream:  step 1 of slab i waits for up[i-1], up[i], up[i+1] (the
-//                    staples reach one t-slice into each neighbour); steps
-//                    2..n follow in stream order, slab by slab; after the
-//                    last step of slab i, event fin[i].
+//                    staples reach one t-slice into each neighbour); after
+//                    the last step of slab i, event fin[i].
 //   download stream: per slab, waits for fin[i], transposes the slab back into
 //                    the staging buffer and copies it to the host.
-// Step k of a slab reads field (k-1)%2 and writes field k%2; stream order
-// runs step k of every slab before step k+1 of any, which covers both the
-// reads of step k+1 and the overwrite of field (k+1)%2 by step k+1.
+// Step k of a slab reads field (k-1)%2 and writes field k%2, so (k, i) must
+// follow (k-1, j) for the slabs j next to i (their reads of field k%2 and
+// the values it reads).  The compute stream runs the (step, slab) items in
+// the order of the key 2k + d(i), d(i) the cyclic distance of slab i from
+// slab 0: neighbouring slabs differ by at most 1 in d, so every item comes
+// after those it depends on, and the wavefront lets slab 0 reach its last
+// step about d_max / 2 steps before the farthest slab, which spreads the
+// downloads over the last steps instead of after them.  Uploads go in the
+// order of d as well.
 // (Winter, "Accelerating QDP++ using GPUs", Sec. 4.3 moves whole fields
 // between host and device on demand; here the device layout stays fixed and
 // the transfers run behind the arithmetic.)
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "lq_internal.h"
@@ -32,9 +40,16 @@ struct Streams {
     if (up) cudaStreamDestroy(up);
     if (down) cudaStreamDestroy(down);
   }
+  // The transfer streams get the highest priority: their transposes are short
+  // and must not queue behind the tens of thousands of pending blocks of a
+  // step kernel (the block scheduler serves higher-priority streams first).
   lq_status make(int n_events) {
-    lq_status st = cuda_check(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking), "upload stream");
-    if (st == LQ_OK) st = cuda_check(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking), "download stream");
+    int least = 0, greatest = 0;
+    lq_status st = cuda_check(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+    if (st == LQ_OK)
+      st = cuda_check(cudaStreamCreateWithPriority(&up, cudaStreamNonBlocking, greatest), "upload stream");
+    if (st == LQ_OK)
+      st = cuda_check(cudaStreamCreateWithPriority(&down, cudaStreamNonBlocking, greatest), "download stream");
     for (int i = 0; i < n_events && st == LQ_OK; ++i) {
       cudaEvent_t e;
       st = cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "pipeline event");
@@ -45,9 +60,70 @@ struct Streams {
 };
 
 int slab_count(int Lt, int n_chunks) {
-  int nc = n_chunks > 0 ? n_chunks : 8;
+  int nc = n_chunks > 0 ? n_chunks : 16;
   return nc > Lt ? Lt : nc;
 }
+
+int cyclic_distance(int i, int nc) { return std::min(i, nc - i); }
+
+// Optional timeline: with LQ_PIPELINE_TRACE=<file>, timing events are recorded
+// around every copy, transpose and step launch, and one line per operation
+// ("what slab step start_ms end_ms", relative to the call's start on the
+// compute stream) is appended to <file> after the call has synchronised.
+struct Trace {
+  const char* path = nullptr;
+  cudaEvent_t t0 = nullptr;
+  struct Op {
+    char what[12];
+    int slab, step;
+    cudaEvent_t a, b;
+  };
+  std::vector<Op> ops;
+  Trace() {
+    path = getenv("LQ_PIPELINE_TRACE");
+    if (path && !*path) path = nullptr;
+  }
+  void begin(cudaStream_t s) {
+    if (!path) return;
+    cudaEventCreate(&t0);
+    cudaEventRecord(t0, s);
+  }
+  int open(const char* what, int slab, int step, cudaStream_t s) {
+    if (!path) return -1;
+    Op o;
+    snprintf(o.what, sizeof(o.what), "%s", what);
+    o.slab = slab;
+    o.step = step;
+    cudaEventCreate(&o.a);
+    cudaEventCreate(&o.b);
+    cudaEventRecord(o.a, s);
+    ops.push_back(o);
+    return (int)ops.size() - 1;
+  }
+  void close(int id, cudaStream_t s) {
+    if (id >= 0) cudaEventRecord(ops[id].b, s);
+  }
+  void write() {
+    if (!path) return;
+    FILE* fp = fopen(path, "a");
+    for (const Op& o : ops) {
+      float a = 0, b = 0;
+      if (fp && cudaEventElapsedTime(&a, t0, o.a) == cudaSuccess && cudaEventElapsedTime(&b, t0, o.b) == cudaSuccess)
+        fprintf(fp, "%s %d %d %.4f %.4f\n", o.what, o.slab, o.step, a, b);
+    }
+    if (fp) {
+      fprintf(fp, "end -1 -1 0 0\n");
+      fclose(fp);
+    }
+  }
+  ~Trace() {
+    for (Op& o : ops) {
+      cudaEventDestroy(o.a);
+      cudaEventDestroy(o.b);
+    }
+    if (t0) cudaEventDestroy(t0);
+  }
+};
 
 }  // namespace
 
@@ -109,6 +185,8 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
   if (st == LQ_OK) st = scratch_alloc(&f[0], bytes, s, "lq_stout_smear_host field");
   if (st == LQ_OK && n_steps > 0) st = scratch_alloc(&f[1], bytes, s, "lq_stout_smear_host work field");
   if (st == LQ_OK) st = scratch_alloc(&stage, bytes, s, "lq_stout_smear_host staging");
+  Trace tr;
+  tr.begin(s);
   // the side streams start after the allocations (and all earlier work) on s
   if (st == LQ_OK) st = cuda_check(cudaEventRecord(start, s), "pipeline start");
   if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(ps.up, start, 0), "pipeline start");
@@ -116,12 +194,21 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
 
   const size_t site_bytes = 4 * 9 * eb;
   const size_t plane = (size_t)V * eb;
-  for (int i = 0; i < nc && st == LQ_OK; ++i) {
+  std::vector<int> by_distance(nc);
+  for (int i = 0; i < nc; ++i) by_distance[i] = i;
+  std::stable_sort(by_distance.begin(), by_distance.end(),
+                   [nc](int a, int b) { return cyclic_distance(a, nc) < cyclic_distance(b, nc); });
+  for (int i : by_distance) {
+    if (st != LQ_OK) break;
     const size_t off = (size_t)sb[i] * site_bytes, len = (size_t)(sb[i + 1] - sb[i]) * site_bytes;
+    int t = tr.open("h2d", i, 0, ps.up);
     st = cuda_check(cudaMemcpyAsync((char*)stage + off, (const char*)host_in + off, len, cudaMemcpyHostToDevice,
                                     ps.up),
                     "lq_stout_smear_host upload");
+    tr.close(t, ps.up);
+    t = tr.open("to_soa", i, 0, ps.up);
     if (st == LQ_OK) st = transpose_range(stage, f[0], g, LQ_LINKS, prec, true, sb[i], sb[i + 1], ps.up);
+    tr.close(t, ps.up);
     // links outside dirs are never written: the work field needs them too
     for (int mu = 0; mu < 4 && st == LQ_OK && n_steps > 0; ++mu)
       if (!((dirs_mask >> mu) & 1u))
@@ -134,39 +221,52 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
     if (st == LQ_OK) st = cuda_check(cudaEventRecord(up[i], ps.up), "pipeline upload event");
   }
 
-  // step 1 in the order 1, 2, ..., nc-1, 0: each slab as soon as it and its
-  // neighbours are resident (slab 0 borders slab nc-1 periodically)
-  std::vector<int> order;
-  for (int i = 1; i < nc; ++i) order.push_back(i);
-  order.push_back(0);
+  // (step, slab) items in wavefront order
+  struct Item {
+    int key, k, i;
+  };
+  std::vector<Item> items;
+  for (int k = 1; k <= n_steps; ++k)
+    for (int i = 0; i < nc; ++i) items.push_back({2 * k + cyclic_distance(i, nc), k, i});
+  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.key < b.key; });
+  std::vector<int> done_order;   // slabs in the order their final field is complete
   if (n_steps == 0)
-    for (int i = 0; i < nc && st == LQ_OK; ++i) st = cuda_check(cudaStreamWaitEvent(s, up[i], 0), "pipeline wait");
-  for (int k = 1; k <= n_steps && st == LQ_OK; ++k) {
-    const void* in = f[(k - 1) % 2];
-    void* out = f[k % 2];
-    for (int i : order) {
-      if (k == 1) {
-        const int nb[3] = {(i + nc - 1) % nc, i, (i + 1) % nc};
-        for (int j : nb)
-          if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(s, up[j], 0), "pipeline wait");
-      }
-      if (st == LQ_OK) st = stout_step_range(in, out, g, prec, rho, dirs_mask, reproject, tc, sb[i], sb[i + 1], s);
-      if (st == LQ_OK && k == n_steps) st = cuda_check(cudaEventRecord(fin[i], s), "pipeline final event");
-      if (st != LQ_OK) break;
+    for (int i : by_distance) {
+      if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(s, up[i], 0), "pipeline wait");
+      if (st == LQ_OK) st = cuda_check(cudaEventRecord(fin[i], s), "pipeline final event");
+      done_order.push_back(i);
+    }
+  for (const Item& it : items) {
+    if (st != LQ_OK) break;
+    const int k = it.k, i = it.i;
+    if (k == 1) {
+      const int nb[3] = {(i + nc - 1) % nc, i, (i + 1) % nc};
+      for (int j : nb)
+        if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(s, up[j], 0), "pipeline wait");
+    }
+    const int t = tr.open("step", i, k, s);
+    if (st == LQ_OK)
+      st = stout_step_range(f[(k - 1) % 2], f[k % 2], g, prec, rho, dirs_mask, reproject, tc, sb[i], sb[i + 1], s);
+    tr.close(t, s);
+    if (st == LQ_OK && k == n_steps) {
+      st = cuda_check(cudaEventRecord(fin[i], s), "pipeline final event");
+      done_order.push_back(i);
     }
   }
   void* result = f[n_steps % 2];
-  if (n_steps == 0 && st == LQ_OK)
-    for (int i = 0; i < nc && st == LQ_OK; ++i) st = cuda_check(cudaEventRecord(fin[i], s), "pipeline final event");
-  for (int i : order) {
+  for (int i : done_order) {
     if (st != LQ_OK) break;
     const size_t off = (size_t)sb[i] * site_bytes, len = (size_t)(sb[i + 1] - sb[i]) * site_bytes;
     st = cuda_check(cudaStreamWaitEvent(ps.down, fin[i], 0), "pipeline wait");
+    int t = tr.open("to_aos", i, n_steps, ps.down);
     if (st == LQ_OK) st = transpose_range(result, stage, g, LQ_LINKS, prec, false, sb[i], sb[i + 1], ps.down);
+    tr.close(t, ps.down);
+    t = tr.open("d2h", i, n_steps, ps.down);
     if (st == LQ_OK)
       st = cuda_check(cudaMemcpyAsync((char*)host_out + off, (const char*)stage + off, len, cudaMemcpyDeviceToHost,
                                       ps.down),
                       "lq_stout_smear_host download");
+    tr.close(t, ps.down);
   }
   if (st == LQ_OK && plaq_out) {
     lq_field tmp;
@@ -176,7 +276,9 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
     tmp.ptr = result;
     tmp.bytes = bytes;
     tmp.owned = false;
+    const int t = tr.open("plaq", -1, n_steps, s);
     st = lq_plaquette(&tmp, plaq_out, stream);
+    tr.close(t, s);
   }
   // the scratch goes back to the pool in s's order, after the downloads; on
   // an error the side streams may still hold work that s never waited for
@@ -189,6 +291,7 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
   for (void* p : {f[0], f[1], stage})
     if (p) scratch_free(p, s);
   const lq_status st3 = cuda_check(cudaStreamSynchronize(s), "lq_stout_smear_host sync");
+  if (st == LQ_OK && st2 == LQ_OK && st3 == LQ_OK) tr.write();
   if (st != LQ_OK) return st;
   return st2 != LQ_OK ? st2 : st3;
 }

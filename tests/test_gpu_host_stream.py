@@ -34,6 +34,8 @@ def _host(U, prec):
     ((4, 4, 4, 2), 3, ALL, 0),          # fewer slices than the default slab count
     ((4, 4, 3, 1), 2, ALL, 1),          # one slab: its own neighbour
     ((4, 4, 4, 6), 0, ALL, 3),          # no steps: a round trip
+    ((2, 3, 4, 32), 6, ALL, 0),         # 16 slabs, wavefront over 6 steps
+    ((3, 2, 2, 20), 5, SPATIAL, 20),    # one t-slice per slab, odd step count
 ])
 def test_host_stream_matches_device_path(gpu, prec, dims, n, dirs, chunks):
     U = fieldgen.near_identity_su3(dims, 700)
@@ -77,3 +79,33 @@ def test_host_stream_rejects_bad_arguments(gpu):
         lq.stout_smear_host(h, out, dims, lq.LQ_F64, 0.1, 1, n_chunks=-1)
     with pytest.raises(ValueError):
         lq.stout_smear_host(h.reshape(-1)[:10], out, dims, lq.LQ_F64, 0.1, 1)  # wrong size (binding check)
+
+
+def test_host_stream_trace_respects_dependencies(gpu, tmp_path, monkeypatch):
+    """LQ_PIPELINE_TRACE timeline: every operation is recorded once, and on the
+    device clock each step-1 launch starts after its slab's and both
+    neighbours' transposes ended, each step after the previous step of the
+    neighbouring slabs, and each download after the slab's last step."""
+    dims, n, nc = (4, 4, 4, 12), 3, 6
+    path = tmp_path / "trace.txt"
+    monkeypatch.setenv("LQ_PIPELINE_TRACE", str(path))
+    U = fieldgen.near_identity_su3(dims, 702)
+    h = _host(U, lq.LQ_F32)
+    lq.stout_smear_host(h, np.empty_like(h), dims, lq.LQ_F32, 0.1, n, ALL, n_chunks=nc)
+    ops = [ln.split() for ln in path.read_text().splitlines() if not ln.startswith("end")]
+    t = {}
+    for what, slab, step, a, b in ops:
+        t[(what, int(slab), int(step))] = (float(a), float(b))
+    assert sorted({w for w, _, _ in t}) == ["d2h", "h2d", "plaq", "step", "to_aos", "to_soa"]
+    assert len(t) == 4 * nc + n * nc + 1
+    eps = 1e-3   # ms: event resolution
+    for i in range(nc):
+        nb = ((i - 1) % nc, i, (i + 1) % nc)
+        assert t[("to_soa", i, 0)][0] >= t[("h2d", i, 0)][1] - eps
+        for j in nb:
+            assert t[("step", i, 1)][0] >= t[("to_soa", j, 0)][1] - eps
+        for k in range(2, n + 1):
+            for j in nb:
+                assert t[("step", i, k)][0] >= t[("step", j, k - 1)][1] - eps
+        assert t[("to_aos", i, n)][0] >= t[("step", i, n)][1] - eps
+        assert t[("d2h", i, n)][0] >= t[("to_aos", i, n)][1] - eps
