@@ -60,11 +60,11 @@ def ch_flops_per_link(stats):
 # GB300 unit counts: 152 SMs x 2 FP64 FMA lanes (304 per cycle) and x 128 FP32 FMA lanes.
 FP64_FMA_PER_CLK = 304
 FP32_FMA_PER_CLK = 152 * 128
-# FP32 small-case (32^3x64) ncu DRAM bytes per launch of the FP32 step kernel divided by
-# its 8,388,608 link updates, times the 42,467,328 link updates of one 48^3x96 launch
+# Small-case (32^3x64) ncu DRAM bytes per launch of each step kernel divided by its
+# 8,388,608 link updates, times the 42,467,328 link updates of one 48^3x96 launch
 # (traffic grows in proportion to the links); see profiles/.
-TRAFFIC_BYTES_PER_LINK_F32 = (633602560 + 576611328) / 8388608.0
-TRAFFIC_BYTES_PER_LINK_F64 = (2051477760 + 1185383168) / 8388608.0
+TRAFFIC_BYTES_PER_LINK_F32 = (680660224 + 662227200) / 8388608.0
+TRAFFIC_BYTES_PER_LINK_F64 = (2045349000 + 1186751000) / 8388608.0
 
 
 def roofline(kernel_ms, links, prec, hbm_gbs, sm_mhz, ch_flops):
@@ -408,7 +408,7 @@ def main():
                          "plaquette_abs_diff": abs(p32[0] - p64[0])},
             "e2e": {"value": weak_scaling_value(links_per_step, world, e2e_ms * 1e-3), "unit": "link-updates/s",
                     "h2d_bytes_per_step": int(pin_in.numel() * 4), "d2h_bytes_per_step": int(pin_out.numel() * 4),
-                    "ms_per_step": e2e_ms, "call": "lq_stout_smear_host (8 t-slabs, transfers overlapped)",
+                    "ms_per_step": e2e_ms, "call": "lq_stout_smear_host (16 t-slabs, transfers overlapped)",
                     "matches_device_path": e2e_same,
                     "sequential": {"value": weak_scaling_value(links_per_step, world, e2e_seq_ms * 1e-3),
                                    "ms_per_step": e2e_seq_ms,
