@@ -41,7 +41,7 @@ METRIC = "stout link-updates/s"
 # Cayley-Hamilton coefficients (+ FP64 re-projection in the FP32 path).
 BYTES_PER_LINK = {"f32": 144.0, "f64": 288.0}
 MATRIX_FLOPS_PER_LINK = 3019.0
-REPROJECT_FLOPS_PER_LINK = 142.0
+REPROJECT_FLOPS_PER_LINK = 132.0
 # Cayley-Hamilton coefficients: c0 = det Q and c1 = tr(Q^2)/2 (35 flops), then
 # either the closed form (179 more) or the reduced Taylor series of degree
 # 2K+1 by Horner's rule (14 per pair of terms: 14 (K-1) + 7).  K depends on

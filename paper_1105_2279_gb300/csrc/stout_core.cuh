@@ -450,16 +450,31 @@ __device__ __forceinline__ M3<R> expiq_assemble(const QH<R>& q, const QH<R>& q2,
 // SU(3) re-projection in FP64: Gram-Schmidt of rows 0 and 1, row 2 = conj(row0 x row1).
 // Written as FMA chains (norms, row1 - p row0, the cross product) to keep
 // the FP64 instruction count low.
-__device__ __forceinline__ double row_norm2(const cx<double>* r) {
-  double n = r[0].re * r[0].re;
+// |row|^2 - 1, as an FMA chain started from -1.
+__device__ __forceinline__ double row_norm2_m1(const cx<double>* r) {
+  double n = fma(r[0].re, r[0].re, -1.0);
   n = fma(r[0].im, r[0].im, n);
   n = fma(r[1].re, r[1].re, n);
   n = fma(r[1].im, r[1].im, n);
   n = fma(r[2].re, r[2].re, n);
   return fma(r[2].im, r[2].im, n);
 }
+
+// 1/sqrt(1 + d).  The rows of a link that is unitary to FP32 rounding have
+// |d| ~ 1e-7; for |d| <= 2^-16 the Taylor polynomial 1 - d/2 + 3d^2/8
+// (- 5d^3/16) is exact to 5|d|^3/16 < 1.2e-15 (to 35 d^4/128 < 1.5e-20 with
+// the cubic term, NR >= 2): two or three FMAs instead of a Newton iteration.
+// Larger |d| (a far from unitary input) takes the Newton path.
+template <int NR> __device__ __forceinline__ double rsqrt_1p(double d) {
+  if ((__double_as_longlong(d) & 0x7fffffffffffffffLL) <= dbl_bits(1.52587890625e-05)) {
+    if (NR == 1) return fma(d, fma(d, 0.375, -0.5), 1.0);
+    return fma(d, fma(d, fma(d, -0.3125, 0.375), -0.5), 1.0);
+  }
+  return rsqrt_nr<NR>(1.0 + d);
+}
+
 template <int NR = 2> __device__ __forceinline__ void reproject_f64(M3<double>& m) {
-  const double r0 = rsqrt_nr<NR>(row_norm2(&m.e[0]));
+  const double r0 = rsqrt_1p<NR>(row_norm2_m1(&m.e[0]));
 #pragma unroll
   for (int k = 0; k < 3; ++k) m.e[k] = cscale(m.e[k], r0);
   // p = sum_k conj(row0_k) row1_k;  row1 <- row1 - p row0
@@ -471,7 +486,7 @@ template <int NR = 2> __device__ __forceinline__ void reproject_f64(M3<double>& 
   const cx<double> mp = mkc(-p.re, -p.im);
 #pragma unroll
   for (int k = 0; k < 3; ++k) m.e[3 + k] = cfma(mp, m.e[k], m.e[3 + k]);
-  const double r1 = rsqrt_nr<NR>(row_norm2(&m.e[3]));
+  const double r1 = rsqrt_1p<NR>(row_norm2_m1(&m.e[3]));
 #pragma unroll
   for (int k = 0; k < 3; ++k) m.e[3 + k] = cscale(m.e[3 + k], r1);
   // row2 = conj(row0 x row1), each entry a*b - c*d as one product and one complex FMA

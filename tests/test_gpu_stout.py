@@ -242,3 +242,21 @@ def test_largest_volumes_pure_gauge_fixed_point(gpu, prec, dims):
     del f, t
     torch.cuda.empty_cache()
     lq.free_all()
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F32, lq.LQ_F64])
+@pytest.mark.parametrize("scale", [1.0, 1.02])
+def test_reprojection(gpu, prec, scale):
+    """FP64 re-projection after each step: links come out in SU(3) (rows
+    orthonormal, det 1) whether the rows enter unitary to rounding (the
+    polynomial normalisation) or 2 % off (the Newton path), and on unitary
+    input it moves the FP32 links by no more than their rounding."""
+    dims = (4, 3, 4, 5)
+    U = fieldgen.near_identity_su3(dims, 710) * scale
+    got = _run(U, prec, 0.1, 2, ALL, reproject=True).astype(np.complex128)
+    du, dd = unitarity_violation(got)
+    tol = 5e-7 if prec == lq.LQ_F32 else 1e-14
+    assert du < tol and dd < tol, (du, dd)
+    if scale == 1.0:
+        plain = _run(U, prec, 0.1, 2, ALL, reproject=False).astype(np.complex128)
+        assert np.max(np.abs(got - plain)) < (1e-6 if prec == lq.LQ_F32 else 1e-14)
