@@ -69,19 +69,61 @@ def batch64(args, torch, lq, fieldgen):
             "speedup_vs_separate": t_sep / t_graph}
 
 
+# Algorithmic flops per link of the backward (4 smeared directions), counted
+# from its kernels: the local step (staple sum 2484, C and Omega 216, Q 20,
+# Q^2 40, G_E 198, traces 148, M = a1 Q + a2 Q^2 + f1 H + f2 (QH + HQ) 684,
+# G_Omega 30, exp(iQ) 70, E^dag G' 198, G_Omega^dag C 216, K 216), the
+# factored six-term gather (3 directions x 2 groups x (2 products + 3
+# accumulating products) = 6264), and in FP64 the coefficients with their
+# derivatives: 35 + 48 + 24 per differentiated Horner step (2K + 4 steps for
+# series order K, read from lq.stout_ch_stats of the FP64 links).
+BWD_LOCAL_FLOPS = 2484 + 216 + 20 + 40 + 198 + 148 + 684 + 30 + 70 + 198 + 216 + 216
+BWD_GATHER_FLOPS = 6264
+WILSON_GRAD_FLOPS = 2484 + 18
+FORCE_FLOPS = 198 + 30
+
+
 def backward24(args, torch, lq, fieldgen):
+    import bench
     dims = (24, 24, 24, 48)
     V = int(np.prod(dims))
+    n, rho = 3, 0.1
     out = {"metric": "stout force link-updates/s (3 steps, Wilson action)", "unit": "link-updates/s",
            "config": {"workload": "24^3x48, exp(i*0.3*H) links seed 4, 3 stout steps rho=0.1 in 4 dims, beta=6"}}
+    pk = bench.peaks()
     for name, prec in (("f64", lq.LQ_F64), ("f32", lq.LQ_F32)):
         f, _ = _field(lq, fieldgen, dims, 4, prec)
         F = lq.Field(f.geom, lq.LQ_LINKS, prec)
+        stats = lq.stout_ch_stats(f, rho, n, (0, 1, 2, 3))
+        g64 = lq.Field(f.geom, lq.LQ_LINKS, lq.LQ_F64)
+        g64.upload(f.download().astype(np.complex128))
+        stats64 = lq.stout_ch_stats(g64, rho, n, (0, 1, 2, 3))
+        del g64
+        mean_k = stats64[2] / max(1, stats64[1])
+        ch_deriv = 35 + 48 + 24 * (2 * mean_k + 4)
+        fwd_f64 = bench.ch_flops_per_link(stats) + (bench.REPROJECT_FLOPS_PER_LINK if prec == lq.LQ_F32
+                                                     else bench.MATRIX_FLOPS_PER_LINK)
+        algebra = n * (BWD_LOCAL_FLOPS + BWD_GATHER_FLOPS) + WILSON_GRAD_FLOPS + FORCE_FLOPS
+        algebra += 0 if prec == lq.LQ_F64 else n * bench.MATRIX_FLOPS_PER_LINK   # FP32 forward recompute
+        flops64 = n * (ch_deriv + fwd_f64) + (algebra if prec == lq.LQ_F64 else 0)
+        flops32 = 0 if prec == lq.LQ_F64 else algebra
         res = {}
         for every in (1, 3):
-            t = _events(torch, lambda: lq.stout_backward(f, 0.1, 3, (0, 1, 2, 3), F, beta=6.0, checkpoint_every=every),
+            t = _events(torch, lambda: lq.stout_backward(f, rho, n, (0, 1, 2, 3), F, beta=6.0, checkpoint_every=every),
                         args.steps, args.warmup)
-            res[f"checkpoint_every_{every}"] = {"ms": t, "value": 3 * V * 4 / (t * 1e-3)}
+            res[f"checkpoint_every_{every}"] = {"ms": t, "value": n * V * 4 / (t * 1e-3)}
+        t1 = res["checkpoint_every_1"]["ms"] * 1e-3
+        mhz = 2070.0
+        p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
+        p32 = 2.0 * bench.FP32_FMA_PER_CLK * mhz * 1e6
+        res["roofline"] = {"bound": "alu", "pipe": "fp64", "unit": "TFLOP/s",
+                           "fp64_flops_per_link": flops64, "fp32_flops_per_link": flops32,
+                           "achieved": flops64 * 4 * V / t1 / 1e12, "peak": p64 / 1e12,
+                           "frac": flops64 * 4 * V / t1 / p64,
+                           "t_bound_ms": {"fp64": 1e3 * flops64 * 4 * V / p64, "fp32": 1e3 * flops32 * 4 * V / p32},
+                           "peak_source": f"derived: {bench.FP64_FMA_PER_CLK} FP64 FMA/clk x 2 x {mhz:.0f} MHz",
+                           "mean_series_order_fp64_table": mean_k,
+                           "note": "checkpoint_every=1; flops of the forward recompute included"}
         g = lq.Field(f.geom, lq.LQ_LINKS, prec)
         g.tensor.copy_(f.tensor)
         tf = _events(torch, lambda: lq.stout_smear(g, 0.1, 3, (0, 1, 2, 3)), args.steps, args.warmup)

@@ -130,35 +130,23 @@ __global__ void __launch_bounds__(128) k_bwd_staple(const V2<R>* __restrict__ U,
     const int s_pmu = nb_fwd(g, s, c[mu], mu);
     const int s_mmu = nb_bwd(g, s, c[mu], mu);
     const int s_mmu_pa = nb_bwd(g, s_pa, c[mu], mu);  // y - mu + a
+    // the three terms through y+mu, with A = U_mu(y), B = U_a(y+mu):
+    //   (K_mu(y) B + A K_a(y+mu)) U_mu(y+a)^dag + (A B) K_mu(y+a)^dag   (5 products, not 6)
     {
-      // K_mu(y) U_a(y+mu) U_mu(y+a)^dag
-      const M3<R> t = mul_nd(ld<R>(U, V, a, s_pmu), ld<R>(U, V, mu, s_pa));
-      mac_nn(acc, ld<R>(K, V, mu, s), t);
+      const M3<R> A = ld<R>(U, V, mu, s), B = ld<R>(U, V, a, s_pmu);
+      M3<R> T = mul_nn(ld<R>(K, V, mu, s), B);
+      mac_nn(T, A, ld<R>(K, V, a, s_pmu));
+      mac_nd(acc, T, ld<R>(U, V, mu, s_pa));
+      mac_nd(acc, mul_nn(A, B), ld<R>(K, V, mu, s_pa));
     }
+    // the three terms through y-mu, with A = U_mu(y-mu), B = U_a(y-mu):
+    //   (K_mu(y-mu)^dag B + A^dag K_a(y-mu)) U_mu(y-mu+a) + (A^dag B) K_mu(y-mu+a)
     {
-      // K_mu(y-mu)^dag U_a(y-mu) U_mu(y-mu+a)
-      const M3<R> t = mul_nn(ld<R>(U, V, a, s_mmu), ld<R>(U, V, mu, s_mmu_pa));
-      mac_dn(acc, ld<R>(K, V, mu, s_mmu), t);
-    }
-    {
-      // U_mu(y) U_a(y+mu) K_mu(y+a)^dag
-      const M3<R> t = mul_nn(ld<R>(U, V, mu, s), ld<R>(U, V, a, s_pmu));
-      mac_nd(acc, t, ld<R>(K, V, mu, s_pa));
-    }
-    {
-      // U_mu(y-mu)^dag U_a(y-mu) K_mu(y-mu+a)
-      const M3<R> t = mul_dn(ld<R>(U, V, mu, s_mmu), ld<R>(U, V, a, s_mmu));
-      mac_nn(acc, t, ld<R>(K, V, mu, s_mmu_pa));
-    }
-    {
-      // U_mu(y-mu)^dag K_a(y-mu) U_mu(y-mu+a)
-      const M3<R> t = mul_dn(ld<R>(U, V, mu, s_mmu), ld<R>(K, V, a, s_mmu));
-      mac_nn(acc, t, ld<R>(U, V, mu, s_mmu_pa));
-    }
-    {
-      // U_mu(y) K_a(y+mu) U_mu(y+a)^dag
-      const M3<R> t = mul_nn(ld<R>(U, V, mu, s), ld<R>(K, V, a, s_pmu));
-      mac_nd(acc, t, ld<R>(U, V, mu, s_pa));
+      const M3<R> A = ld<R>(U, V, mu, s_mmu), B = ld<R>(U, V, a, s_mmu);
+      M3<R> T = mul_dn(ld<R>(K, V, mu, s_mmu), B);
+      mac_dn(T, A, ld<R>(K, V, a, s_mmu));
+      mac_nn(acc, T, ld<R>(U, V, mu, s_mmu_pa));
+      mac_nn(acc, mul_dn(A, B), ld<R>(K, V, mu, s_mmu_pa));
     }
   }
   st_m3<R>(G + (long long)a * 9 * V + s, V, acc);
