@@ -352,20 +352,22 @@ def main():
         lq.plaquette(f32)
         f32.download_ptr(pin_out.data_ptr())
 
-    def time_e2e(fn):
+    def time_e2e(fn, calls):
         fn()
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e2e_steps):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
+        evs[0].record(stream)
+        for i in range(e2e_steps):
             fn()
-        e1.record(stream)
+            evs[i + 1].record(stream)
         barrier()
-        return max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist)
+        calls.extend(evs[i].elapsed_time(evs[i + 1]) for i in range(e2e_steps))
+        return max_over_ranks(evs[0].elapsed_time(evs[-1]) / e2e_steps, dist)
 
-    e2e_ms = time_e2e(e2e_step)
+    e2e_calls, e2e_seq_calls = [], []
+    e2e_ms = time_e2e(e2e_step, e2e_calls)
     out_pipelined = pin_out.numpy().copy()
-    e2e_seq_ms = time_e2e(e2e_sequential_step)
+    e2e_seq_ms = time_e2e(e2e_sequential_step, e2e_seq_calls)
     # the pipelined call's result is the device path's, bit for bit
     e2e_same = bool(np.array_equal(out_pipelined, pin_out.numpy()))
     del out_pipelined
@@ -408,10 +410,11 @@ def main():
                          "plaquette_abs_diff": abs(p32[0] - p64[0])},
             "e2e": {"value": weak_scaling_value(links_per_step, world, e2e_ms * 1e-3), "unit": "link-updates/s",
                     "h2d_bytes_per_step": int(pin_in.numel() * 4), "d2h_bytes_per_step": int(pin_out.numel() * 4),
-                    "ms_per_step": e2e_ms, "call": "lq_stout_smear_host (16 t-slabs, transfers overlapped)",
+                    "ms_per_step": e2e_ms, "ms_calls": e2e_calls,
+                    "call": "lq_stout_smear_host (16 t-slabs, transfers overlapped)",
                     "matches_device_path": e2e_same,
                     "sequential": {"value": weak_scaling_value(links_per_step, world, e2e_seq_ms * 1e-3),
-                                   "ms_per_step": e2e_seq_ms,
+                                   "ms_per_step": e2e_seq_ms, "ms_calls": e2e_seq_calls,
                                    "call": "lq_field_upload + lq_stout_smear + lq_plaquette + lq_field_download"}},
             "gpu_launches": args.steps * (N_SMEAR + 2),
             "clocks": clocks,

@@ -11,13 +11,13 @@
 //                    the staging buffer and copies it to the host.
 // Step k of a slab reads field (k-1)%2 and writes field k%2, so (k, i) must
 // follow (k-1, j) for the slabs j next to i (their reads of field k%2 and
-// the values it reads).  The compute stream runs the (step, slab) items in
-// the order of the key 2k + d(i), d(i) the cyclic distance of slab i from
-// slab 0: neighbouring slabs differ by at most 1 in d, so every item comes
-// after those it depends on, and the wavefront lets slab 0 reach its last
-// step about d_max / 2 steps before the farthest slab, which spreads the
-// downloads over the last steps instead of after them.  Uploads go in the
-// order of d as well.
+// the values it reads).  The first two and the last two steps run as
+// (step, slab) items in the order of the key 2k + d(i), d(i) the cyclic
+// distance of slab i from slab 0: neighbouring slabs differ by at most 1 in
+// d, so every item comes after those it depends on, and the wavefront lets
+// the slabs near slab 0 finish about d_max / 2 steps before the farthest
+// ones, which spreads the downloads over the last steps.  The steps in
+// between are whole-lattice launches.  Uploads go in the order of d as well.
 // (Winter, "Accelerating QDP++ using GPUs", Sec. 4.3 moves whole fields
 // between host and device on demand; here the device layout stays fixed and
 // the transfers run behind the arithmetic.)
@@ -221,14 +221,28 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
     if (st == LQ_OK) st = cuda_check(cudaEventRecord(up[i], ps.up), "pipeline upload event");
   }
 
-  // (step, slab) items in wavefront order
+  // (step, slab) items: the first two and the last two steps in wavefront
+  // order (they overlap the uploads and the downloads), the steps between as
+  // whole-lattice launches (i = -1), which avoid the per-launch tail and the
+  // cold slab boundaries of slab launches
   struct Item {
     int key, k, i;
   };
   std::vector<Item> items;
-  for (int k = 1; k <= n_steps; ++k)
-    for (int i = 0; i < nc; ++i) items.push_back({2 * k + cyclic_distance(i, nc), k, i});
-  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.key < b.key; });
+  auto wave = [&](int k_lo, int k_hi) {
+    std::vector<Item> w;
+    for (int k = k_lo; k <= k_hi; ++k)
+      for (int i = 0; i < nc; ++i) w.push_back({2 * k + cyclic_distance(i, nc), k, i});
+    std::stable_sort(w.begin(), w.end(), [](const Item& a, const Item& b) { return a.key < b.key; });
+    items.insert(items.end(), w.begin(), w.end());
+  };
+  if (n_steps <= 4) {
+    wave(1, n_steps);
+  } else {
+    wave(1, 2);
+    for (int k = 3; k <= n_steps - 2; ++k) items.push_back({0, k, -1});
+    wave(n_steps - 1, n_steps);
+  }
   std::vector<int> done_order;   // slabs in the order their final field is complete
   if (n_steps == 0)
     for (int i : by_distance) {
@@ -245,8 +259,8 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
         if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(s, up[j], 0), "pipeline wait");
     }
     const int t = tr.open("step", i, k, s);
-    if (st == LQ_OK)
-      st = stout_step_range(f[(k - 1) % 2], f[k % 2], g, prec, rho, dirs_mask, reproject, tc, sb[i], sb[i + 1], s);
+    const long long s0 = i < 0 ? 0 : sb[i], s1 = i < 0 ? V : sb[i + 1];
+    if (st == LQ_OK) st = stout_step_range(f[(k - 1) % 2], f[k % 2], g, prec, rho, dirs_mask, reproject, tc, s0, s1, s);
     tr.close(t, s);
     if (st == LQ_OK && k == n_steps) {
       st = cuda_check(cudaEventRecord(fin[i], s), "pipeline final event");

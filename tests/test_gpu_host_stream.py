@@ -81,12 +81,15 @@ def test_host_stream_rejects_bad_arguments(gpu):
         lq.stout_smear_host(h.reshape(-1)[:10], out, dims, lq.LQ_F64, 0.1, 1)  # wrong size (binding check)
 
 
-def test_host_stream_trace_respects_dependencies(gpu, tmp_path, monkeypatch):
+@pytest.mark.parametrize("n", [3, 6])
+def test_host_stream_trace_respects_dependencies(gpu, tmp_path, monkeypatch, n):
     """LQ_PIPELINE_TRACE timeline: every operation is recorded once, and on the
     device clock each step-1 launch starts after its slab's and both
     neighbours' transposes ended, each step after the previous step of the
-    neighbouring slabs, and each download after the slab's last step."""
-    dims, n, nc = (4, 4, 4, 12), 3, 6
+    neighbouring slabs (or the previous whole-lattice launch: with more than
+    four steps, the middle steps run whole, slab -1), and each download after
+    the slab's last step."""
+    dims, nc = (4, 4, 4, 12), 6
     path = tmp_path / "trace.txt"
     monkeypatch.setenv("LQ_PIPELINE_TRACE", str(path))
     U = fieldgen.near_identity_su3(dims, 702)
@@ -97,15 +100,22 @@ def test_host_stream_trace_respects_dependencies(gpu, tmp_path, monkeypatch):
     for what, slab, step, a, b in ops:
         t[(what, int(slab), int(step))] = (float(a), float(b))
     assert sorted({w for w, _, _ in t}) == ["d2h", "h2d", "plaq", "step", "to_aos", "to_soa"]
-    assert len(t) == 4 * nc + n * nc + 1
+    whole = set(range(3, n - 1)) if n > 4 else set()
+    assert len(t) == 4 * nc + (n - len(whole)) * nc + len(whole) + 1
     eps = 1e-3   # ms: event resolution
+
+    def end_of(k, slabs):
+        return max(t[("step", -1, k)][1] if k in whole else t[("step", j, k)][1] for j in slabs)
+
+    for k in whole:
+        assert t[("step", -1, k)][0] >= end_of(k - 1, range(nc)) - eps
     for i in range(nc):
         nb = ((i - 1) % nc, i, (i + 1) % nc)
         assert t[("to_soa", i, 0)][0] >= t[("h2d", i, 0)][1] - eps
         for j in nb:
             assert t[("step", i, 1)][0] >= t[("to_soa", j, 0)][1] - eps
         for k in range(2, n + 1):
-            for j in nb:
-                assert t[("step", i, k)][0] >= t[("step", j, k - 1)][1] - eps
+            if k not in whole:
+                assert t[("step", i, k)][0] >= end_of(k - 1, nb) - eps
         assert t[("to_aos", i, n)][0] >= t[("step", i, n)][1] - eps
         assert t[("d2h", i, n)][0] >= t[("to_aos", i, n)][1] - eps
