@@ -35,7 +35,7 @@ SEED = 2
 WORKLOAD = "48^3x96 periodic, exp(i*0.3*H) links seed 2, 6 stout steps rho=0.125 in 4 dirs + plaquette"
 METRIC = "stout link-updates/s"
 
-# Algorithmic counts per link update (4 smeared directions), derived in the design doc:
+# Algorithmic counts per link update (4 smeared directions):
 # minimum traffic = read every link once + write every updated link once;
 # flops of the staple / Omega / Q / exp / U' matrix algebra, and of the FP64
 # Cayley-Hamilton coefficients (+ FP64 re-projection in the FP32 path).
