@@ -67,25 +67,36 @@ TRAFFIC_BYTES_PER_LINK_F32 = (680660224 + 662227200) / 8388608.0
 TRAFFIC_BYTES_PER_LINK_F64 = (2045349000 + 1186751000) / 8388608.0
 
 
-def roofline(kernel_ms, links, prec, hbm_gbs, sm_mhz, ch_flops):
-    """Roofline of one step-kernel launch: time bound of each resource from the
-    algorithmic counts, the binding one reported as achieved / peak."""
-    f64_flops = ch_flops + (REPROJECT_FLOPS_PER_LINK if prec == "f32" else MATRIX_FLOPS_PER_LINK)
-    f32_flops = MATRIX_FLOPS_PER_LINK if prec == "f32" else 0.0
+# The two-link product variant (3) forms each U_mu(y) U_nu(y+mu) once: 9 staple
+# products per link instead of 12, for W written once and read once per link
+# on top of the links (12 colour matrices per site over 4 links).
+W_SAVED_FLOPS_PER_LINK = 3 * 198.0
+W_BYTES_PER_LINK = {"f32": 2 * 3 * 72.0, "f64": 2 * 3 * 144.0}
+
+
+def roofline(kernel_ms, links, prec, hbm_gbs, sm_mhz, ch_flops, variant=1):
+    """Roofline of one step (its one or two kernel launches): time bound of each
+    resource from the algorithmic counts, the binding one reported as achieved / peak."""
+    matrix = MATRIX_FLOPS_PER_LINK - (W_SAVED_FLOPS_PER_LINK if variant == 3 else 0.0)
+    f64_flops = ch_flops + (REPROJECT_FLOPS_PER_LINK if prec == "f32" else matrix)
+    f32_flops = matrix if prec == "f32" else 0.0
+    nbytes = BYTES_PER_LINK[prec] + (W_BYTES_PER_LINK[prec] if variant == 3 else 0.0)
     p64 = 2.0 * FP64_FMA_PER_CLK * sm_mhz * 1e6
     p32 = 2.0 * FP32_FMA_PER_CLK * sm_mhz * 1e6
-    t = {"hbm": BYTES_PER_LINK[prec] * links / (hbm_gbs * 1e9), "fp64": f64_flops * links / p64,
+    t = {"hbm": nbytes * links / (hbm_gbs * 1e9), "fp64": f64_flops * links / p64,
          "fp32": f32_flops * links / p32}
     sec = kernel_ms * 1e-3
     ach64 = f64_flops * links / sec / 1e12
-    traffic = (TRAFFIC_BYTES_PER_LINK_F32 if prec == "f32" else TRAFFIC_BYTES_PER_LINK_F64) * links
+    # ncu DRAM counts were taken on the one-kernel step
+    traffic = None if variant != 1 else (
+        (TRAFFIC_BYTES_PER_LINK_F32 if prec == "f32" else TRAFFIC_BYTES_PER_LINK_F64) * links)
     return {"bound": "alu", "pipe": "fp64", "achieved": ach64, "peak": p64 / 1e12, "unit": "TFLOP/s",
             "frac": ach64 / (p64 / 1e12), "traffic": traffic,
             "peak_source": f"derived: {FP64_FMA_PER_CLK} FP64 FMA/clk x 2 flops x {sm_mhz:.0f} MHz median SM clock",
             "fp64_flops_per_link": f64_flops, "ch_flops_per_link": ch_flops, "fp32_flops_per_link": f32_flops,
-            "bytes_per_link": BYTES_PER_LINK[prec], "kernel_ms": kernel_ms,
+            "bytes_per_link": nbytes, "kernel_ms": kernel_ms,
             "t_bound_ms": {k: 1e3 * v for k, v in t.items()},
-            "hbm_frac": BYTES_PER_LINK[prec] * links / sec / 1e9 / hbm_gbs}
+            "hbm_frac": nbytes * links / sec / 1e9 / hbm_gbs}
 
 
 def peaks():
@@ -276,9 +287,10 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def timed(field, steps, warmup):
+    def timed(field, steps, warmup, opts=None):
         field.upload(U_host)
-        opts = smear_opts if field.prec == lq.LQ_F32 or args.variant != 2 else {}
+        if opts is None:
+            opts = smear_opts if field.prec == lq.LQ_F32 or args.variant != 2 else {}
         for _ in range(warmup):
             lq.stout_smear(field, RHO, N_SMEAR, DIRS, **opts)
             lq.plaquette(field)
@@ -307,6 +319,8 @@ def main():
     with ClockSampler(local) as clk:
         step32, kern32 = timed(f32, args.steps, args.warmup)
         step64, kern64 = timed(f64, args.f64_steps, 1)
+        # FP64 with the two-link product staples (variant 3, requested explicitly)
+        step64w, kern64w = timed(f64, args.f64_steps, 1, {"variant": 3})
     clocks = clk.summary()
 
     # accuracy at the stated precision: fresh inputs, one 6-step smearing each
@@ -325,8 +339,12 @@ def main():
     d32 = f32.download()
     d64 = f64.download()
     err_32_64 = float(np.max(np.abs(d32.astype(np.complex128) - d64)))
+    f64.upload(U_host)
+    lq.stout_smear(f64, RHO, N_SMEAR, DIRS, variant=3)
+    d64w = f64.download()
+    err_w_64 = float(np.max(np.abs(d64w - d64)))
     rng = np.random.default_rng(7)
-    e32o, e64o = 0.0, 0.0
+    e32o, e64o, e64wo = 0.0, 0.0, 0.0
     if rank == 0:
         for _ in range(3):
             c = [int(rng.integers(L)) for L in DIMS]
@@ -334,7 +352,8 @@ def main():
                 N_SMEAR, N_SMEAR, N_SMEAR, N_SMEAR]
             e32o = max(e32o, float(np.max(np.abs(d32[c[3], c[2], c[1], c[0]] - ref))))
             e64o = max(e64o, float(np.max(np.abs(d64[c[3], c[2], c[1], c[0]] - ref))))
-    del d32, d64
+            e64wo = max(e64wo, float(np.max(np.abs(d64w[c[3], c[2], c[1], c[0]] - ref))))
+    del d32, d64, d64w
 
     # end to end through the C ABI with host buffers (page-locked): links in host memory ->
     # smeared links + plaquette in host memory, one lq_stout_smear_host call per step (the
@@ -353,7 +372,8 @@ def main():
         f32.download_ptr(pin_out.data_ptr())
 
     def time_e2e(fn, calls):
-        fn()
+        for _ in range(3):   # warm-up: the GPU idled during the CPU-side accuracy sampling
+            fn()
         barrier()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps + 1)]
         evs[0].record(stream)
@@ -383,18 +403,24 @@ def main():
         value64 = weak_scaling_value(links_per_step, world, step64 * 1e-3)
         links_per_launch = V * len(DIRS)
         mhz = clocks.get("sm_mhz") or 2070.0
-        roof32 = roofline(kern32, links_per_launch, "f32", hbm, mhz, ch_flops_per_link(ch32))
-        roof32["ch_stats"] = {"link_updates": ch32[0], "series": ch32[1], "mean_K": ch32[2] / max(1, ch32[1])}
+        kernel_names = {1: "k_stout_global_f{b}", 2: "k_stout_smem<float,reproject>",
+                        3: "k_wfield<{t}> + k_stout_wf<{t}>"}
         tuned32 = lq.tune_lookup(lq.LQ_F32, DIMS, DIRS)
         var32 = args.variant or (tuned32[2] if tuned32 else 1)
-        roof32["kernel"] = "k_stout_smem<float,reproject>" if var32 == 2 else "k_stout_global_f32<reproject>"
+        roof32 = roofline(kern32, links_per_launch, "f32", hbm, mhz, ch_flops_per_link(ch32), var32)
+        roof32["ch_stats"] = {"link_updates": ch32[0], "series": ch32[1], "mean_K": ch32[2] / max(1, ch32[1])}
+        roof32["kernel"] = kernel_names[var32].format(b="32<reproject>", t="float")
         roof32["launch"] = {"variant": var32, "tuned": tuned32}
         if var32 == 2:
             roof32["traffic"] = None   # DRAM counters of the shared-memory kernel not captured at this revision
-        roof64 = roofline(kern64, links_per_launch, "f64", hbm, mhz, ch_flops_per_link(ch64))
+        tuned64 = lq.tune_lookup(lq.LQ_F64, DIMS, DIRS)
+        var64 = (args.variant if args.variant in (1, 3) else 0) or (tuned64[2] if tuned64 else 1)
+        roof64 = roofline(kern64, links_per_launch, "f64", hbm, mhz, ch_flops_per_link(ch64), var64)
         roof64["ch_stats"] = {"link_updates": ch64[0], "series": ch64[1], "mean_K": ch64[2] / max(1, ch64[1])}
-        roof64["kernel"] = "k_stout_global_f64"
-        roof64["launch"] = {"variant": 1, "tuned": lq.tune_lookup(lq.LQ_F64, DIMS, DIRS)}
+        roof64["kernel"] = kernel_names[var64].format(b="64", t="double")
+        roof64["launch"] = {"variant": var64, "tuned": tuned64}
+        roof64w = roofline(kern64w, links_per_launch, "f64", hbm, mhz, ch_flops_per_link(ch64), 3)
+        roof64w["kernel"] = kernel_names[3].format(t="double")
         out = {
             "metric": METRIC, "value": value, "unit": "link-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step32, "higher_is_better": True, "scaling": "weak",
@@ -404,6 +430,11 @@ def main():
                        "l2": "inputs larger than L2 (3.06 GB FP32 links)", "per_rank": "independent lattice per rank"},
             "roofline": roof32,
             "fp64": {"value": value64, "ms_per_step": step64, "kernel_ms": kern64, "roofline": roof64},
+            "fp64_two_link_products": {
+                "value": weak_scaling_value(links_per_step, world, step64w * 1e-3), "ms_per_step": step64w,
+                "kernel_ms": kern64w, "roofline": roof64w, "vs_oracle_sampled_max_abs": e64wo,
+                "vs_fp64_one_kernel_max_abs": err_w_64,
+                "note": "opts variant=3: k_wfield + k_stout_wf, 9 staple products per link instead of 12"},
             "fp32_speedup_vs_fp64": value / value64,
             "accuracy": {"fp32_vs_fp64_gpu_max_abs": err_32_64, "fp32_vs_oracle_sampled_max_abs": e32o,
                          "fp64_vs_oracle_sampled_max_abs": e64o, "plaquette_fp32": p32[0], "plaquette_fp64": p64[0],

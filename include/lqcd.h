@@ -216,7 +216,15 @@ typedef struct lq_stout_opts {
   int use_graph;          /* 1: record the n-step launch sequence as a CUDA graph
                              and replay it (cached per field, dims, n, rho, dirs)   */
   int variant;            /* 0 tuned/default, 1 global-load kernel,
-                             2 shared-memory staged kernel                           */
+                             2 shared-memory staged kernel (FP32 links),
+                             3 two kernels per step: the two-link products
+                               U_mu(y) U_nu(y+mu) of every ordered pair of smeared
+                               directions, then the staples from them (9 products
+                               per link instead of 12; a scratch buffer of
+                               |dirs|(|dirs|-1) colour-matrix fields).  Variants 0-2
+                               give bit-identical links; variant 3 associates the
+                               staple products differently (equal to rounding), so
+                               the tuner never picks it: it is requested here.      */
   int block;              /* threads per block (N_threads, [W] Sec. 4.4); 0 = tuned  */
   int sites_per_thread;   /* N_site ([W] Sec. 4.4); 0 = tuned                        */
   void* work;             /* optional device workspace of >= one links field;

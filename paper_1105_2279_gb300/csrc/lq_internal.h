@@ -95,9 +95,10 @@ bool tune_get(const char* kernel, int prec, const int dims[4], unsigned dirs, Tu
 void tune_put(const char* kernel, int prec, const int dims[4], unsigned dirs, const TuneChoice& c);
 
 // Stout internals shared with the backward and batch translation units.
+// wbuf: two-link product buffer for variant 3 (NULL: allocated per call when needed)
 lq_status stout_run_steps(void* links, void* work, const lq_geom& g, int prec, double rho,
                           int n_steps, unsigned dirs, int reproject, const TuneChoice& tc,
-                          cudaStream_t s);
+                          cudaStream_t s, void* wbuf = nullptr);
 TuneChoice stout_default_choice(int prec);
 // One stout step over the sites [s_begin, s_end) only (global-load kernel).
 lq_status stout_step_range(const void* in, void* out, const lq_geom& g, int prec, double rho, unsigned dirs,

@@ -65,6 +65,7 @@ extern "C" lq_status lq_stout_smear_noalloc(lq_field* links, double rho, int n_s
   // tuned launch shape if one is cached; never runs the tuner (it allocates)
   TuneChoice tc = stout_default_choice(links->prec);
   if (tune_enabled()) tune_get("stout", links->prec, links->geom.dims, dirs_mask, &tc);
+  if (tc.variant == 3) tc = stout_default_choice(links->prec);   // variant 3 needs a product buffer
   const int reproject = links->prec == LQ_F32 ? 1 : 0;
   return stout_run_steps(links->ptr, work, links->geom, links->prec, rho, n_steps, dirs_mask, reproject, tc,
                          as_stream(stream));

@@ -183,6 +183,86 @@ __global__ void __launch_bounds__(kSmemThreads, 1) k_stout_smem(const typename v
 
 static size_t smem_bytes_f32() { return (size_t)3 * 36 * kSmemHS * sizeof(float2); }
 
+// Variant 3: two kernels per step.  The two-link products
+//   W_{mu nu}(y) = U_mu(y) U_nu(y + mu)
+// of every ordered pair of smeared directions are formed once per step (one
+// product each), and each serves two staples:
+//   upper staple of (x, mu) in plane nu = W_{nu mu}(x) U_nu(x + mu)^dag
+//   lower staple of (x, mu) in plane nu = U_nu(x - nu)^dag W_{mu nu}(x - nu)
+// so a link's six staples cost 6 + 3 products (3 W per link on average)
+// instead of 12, for W read and written through HBM.  For FP64 links,
+// whose step is bound by the FP64 pipe.
+struct PairMap {
+  int idx[16];   // idx[4 mu + nu]: W plane of the ordered pair (mu, nu), -1 if unused
+  int mu[12], nu[12];
+  int n;
+};
+
+static PairMap pair_map(unsigned dirs) {
+  PairMap pm;
+  pm.n = 0;
+  for (int i = 0; i < 16; ++i) pm.idx[i] = -1;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      if (a != b && ((dirs >> a) & 1u) && ((dirs >> b) & 1u)) {
+        pm.idx[4 * a + b] = pm.n;
+        pm.mu[pm.n] = a;
+        pm.nu[pm.n] = b;
+        ++pm.n;
+      }
+  return pm;
+}
+
+static size_t wfield_bytes(const lq_geom& g, int prec, unsigned dirs) {
+  return (size_t)pair_map(dirs).n * 9 * (size_t)g.volume * elem_bytes(LQ_LINKS, prec);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_wfield(const typename vec2<R>::type* __restrict__ U,
+                                                typename vec2<R>::type* __restrict__ W, GeomArgs g, PairMap pm) {
+  const long long V = g.V;
+  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const int s = (int)sl;
+  const int p = blockIdx.y;
+  const int mu = pm.mu[p], nu = pm.nu[p];
+  int c[4];
+  site_coords(g, s, c);
+  const int s_pmu = nb_fwd(g, s, coord_of(c, mu), mu);
+  st_m3<R>(W + (long long)p * 9 * V + s, V, mul_nn(ld_link<R>(U, V, mu, s), ld_link<R>(U, V, nu, s_pmu)));
+}
+
+template <typename R, bool REPRO>
+__global__ void __launch_bounds__(256) k_stout_wf(const typename vec2<R>::type* __restrict__ Uin,
+                                                  const typename vec2<R>::type* __restrict__ W,
+                                                  typename vec2<R>::type* __restrict__ Uout, GeomArgs g, R rho,
+                                                  unsigned dirs, int nd, MuList ml, PairMap pm) {
+  const int mi = blockIdx.x % nd;
+  const long long sl = (long long)(blockIdx.x / nd) * blockDim.x + threadIdx.x;
+  const long long V = g.V;
+  if (sl >= V) return;
+  const int mu = mi == 0 ? ml.mu[0] : (mi == 1 ? ml.mu[1] : (mi == 2 ? ml.mu[2] : ml.mu[3]));
+  const int s = (int)sl;
+  int c[4];
+  site_coords(g, s, c);
+  const int s_pmu = nb_fwd(g, s, coord_of(c, mu), mu);
+  M3<R> S;
+  m_zero(S);
+#pragma unroll 1
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu || !((dirs >> nu) & 1u)) continue;
+    const int cn = coord_of(c, nu);
+    const int Ln = nu == 0 ? g.L[0] : (nu == 1 ? g.L[1] : (nu == 2 ? g.L[2] : g.L[3]));
+    const int sn = nu == 0 ? g.stride[0] : (nu == 1 ? g.stride[1] : (nu == 2 ? g.stride[2] : g.stride[3]));
+    const int s_mnu = (cn > 0) ? s - sn : s + (Ln - 1) * sn;
+    const int p_up = pm.idx[4 * nu + mu], p_lo = pm.idx[4 * mu + nu];
+    mac_nd(S, ld_m3<R>(W + (long long)p_up * 9 * V + s, V), ld_link<R>(Uin, V, nu, s_pmu));
+    mac_dn(S, ld_link<R>(Uin, V, nu, s_mnu), ld_m3<R>(W + (long long)p_lo * 9 * V + s_mnu, V));
+  }
+  const M3<R> Up = stout_update<R>(S, ld_link<R>(Uin, V, mu, s), rho, REPRO);
+  st_m3<R>(Uout + (long long)mu * 9 * V + s, V, Up);
+}
+
 static MuList mu_list(unsigned dirs, int* n) {
   MuList m;
   int k = 0;
@@ -226,15 +306,40 @@ static lq_status launch_global(const void* in, void* out, const GeomArgs& g, int
 lq_status stout_step_range(const void* in, void* out, const lq_geom& geom, int prec, double rho, unsigned dirs,
                            int reproject, const TuneChoice& tc, long long s_begin, long long s_end, cudaStream_t s) {
   TuneChoice t = tc;
-  if (t.variant == 2) t = stout_default_choice(prec);   // the shared-memory variant tiles whole lattices
+  if (t.variant != 1) t = stout_default_choice(prec);   // variants 2 and 3 work on whole lattices
   return launch_global(in, out, geom_args(geom), prec, rho, dirs, reproject, t, s_begin, s_end, s);
 }
 
 static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int prec, double rho,
-                             unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s) {
+                             unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s,
+                             void* wbuf = nullptr) {
   const GeomArgs g = geom_args(geom);
   int nd = 0;
   const MuList ml = mu_list(dirs, &nd);
+  if (tc.variant == 3 && wbuf) {
+    const PairMap pm = pair_map(dirs);
+    const unsigned gs = (unsigned)((g.V + 127) / 128);
+    const int block = tc.block > 0 ? tc.block : 128;
+    const dim3 grid((unsigned)(((g.V + block - 1) / block) * nd));
+    if (prec == LQ_F64) {
+      k_wfield<double><<<dim3(gs, pm.n), 128, 0, s>>>((const double2*)in, (double2*)wbuf, g, pm);
+      if (reproject)
+        k_stout_wf<double, true><<<grid, block, 0, s>>>((const double2*)in, (const double2*)wbuf, (double2*)out, g,
+                                                        rho, dirs, nd, ml, pm);
+      else
+        k_stout_wf<double, false><<<grid, block, 0, s>>>((const double2*)in, (const double2*)wbuf, (double2*)out, g,
+                                                         rho, dirs, nd, ml, pm);
+    } else {
+      k_wfield<float><<<dim3(gs, pm.n), 128, 0, s>>>((const float2*)in, (float2*)wbuf, g, pm);
+      if (reproject)
+        k_stout_wf<float, true><<<grid, block, 0, s>>>((const float2*)in, (const float2*)wbuf, (float2*)out, g,
+                                                       (float)rho, dirs, nd, ml, pm);
+      else
+        k_stout_wf<float, false><<<grid, block, 0, s>>>((const float2*)in, (const float2*)wbuf, (float2*)out, g,
+                                                        (float)rho, dirs, nd, ml, pm);
+    }
+    return launch_check("stout step kernels (two-link product variant)");
+  }
   if (tc.variant == 2 && prec == LQ_F32) {
     static bool attr_set[64] = {false};
     const int dev = current_device();
@@ -265,9 +370,25 @@ static size_t dir_block_bytes(const lq_geom& g, int prec) {
   return (size_t)g.volume * 9 * elem_bytes(LQ_LINKS, prec);
 }
 
+static lq_status stout_run_steps_impl(void* links, void* work, const lq_geom& g, int prec, double rho, int n_steps,
+                                      unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s, void* wbuf);
+
 lq_status stout_run_steps(void* links, void* work, const lq_geom& g, int prec, double rho, int n_steps,
-                          unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s) {
+                          unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s, void* wbuf) {
   if (n_steps <= 0) return LQ_OK;
+  void* own_w = nullptr;
+  if (tc.variant == 3 && !wbuf) {
+    lq_status st = scratch_alloc(&own_w, wfield_bytes(g, prec, dirs), s, "stout two-link products");
+    if (st != LQ_OK) return st;
+    wbuf = own_w;
+  }
+  lq_status st = stout_run_steps_impl(links, work, g, prec, rho, n_steps, dirs, reproject, tc, s, wbuf);
+  if (own_w) scratch_free(own_w, s);
+  return st;
+}
+
+static lq_status stout_run_steps_impl(void* links, void* work, const lq_geom& g, int prec, double rho, int n_steps,
+                                      unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s, void* wbuf) {
   const size_t db = dir_block_bytes(g, prec);
   // links outside `dirs` are never written: give the work buffer a copy once
   for (int mu = 0; mu < 4; ++mu)
@@ -280,7 +401,7 @@ lq_status stout_run_steps(void* links, void* work, const lq_geom& g, int prec, d
   for (int k = 0; k < n_steps; ++k) {
     const void* in = (k % 2 == 0) ? links : work;
     void* out = (k % 2 == 0) ? work : links;
-    lq_status st = launch_step(in, out, g, prec, rho, dirs, reproject, tc, s);
+    lq_status st = launch_step(in, out, g, prec, rho, dirs, reproject, tc, s, wbuf);
     if (st != LQ_OK) return st;
   }
   if (n_steps % 2 == 1) {
@@ -372,6 +493,9 @@ lq_status stout_choose(const lq_field* f, double rho, unsigned dirs, int reproje
     if (out->variant == 2) {
       out->block = kSmemThreads;
       out->nsite = o->sites_per_thread > 0 ? o->sites_per_thread : 8;  // t-slices per CTA
+    } else if (out->variant == 3) {
+      out->block = o->block > 0 ? o->block : 128;
+      out->nsite = 1;
     } else {
       out->block = o->block > 0 ? o->block : 128;
       out->nsite = o->sites_per_thread > 0 ? o->sites_per_thread : 1;
@@ -402,6 +526,7 @@ struct GraphKey {
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   void* work = nullptr;
+  void* wfield = nullptr;   // two-link products (variant 3)
 };
 static std::mutex g_graph_mu;
 static std::map<GraphKey, GraphEntry>& graph_cache() {
@@ -413,6 +538,7 @@ static void release_graphs() {
   for (auto& kv : graph_cache()) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (kv.second.work) cudaFree(kv.second.work);
+    if (kv.second.wfield) cudaFree(kv.second.wfield);
   }
   graph_cache().clear();
 }
@@ -439,6 +565,13 @@ static lq_status run_graph(lq_field* f, double rho, int n, unsigned dirs, int re
     GraphEntry e;
     lq_status st = cuda_check(cudaMalloc(&e.work, f->bytes), "stout graph workspace");
     if (st != LQ_OK) return st;
+    if (tc.variant == 3) {
+      st = cuda_check(cudaMalloc(&e.wfield, wfield_bytes(f->geom, f->prec, dirs)), "stout graph two-link products");
+      if (st != LQ_OK) {
+        cudaFree(e.work);
+        return st;
+      }
+    }
     cudaStream_t cap;
     st = cuda_check(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "stout graph stream");
     if (st != LQ_OK) {
@@ -448,7 +581,7 @@ static lq_status run_graph(lq_field* f, double rho, int n, unsigned dirs, int re
     cudaGraph_t graph = nullptr;
     st = cuda_check(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "stout graph capture");
     if (st == LQ_OK) {
-      lq_status st_run = stout_run_steps(f->ptr, e.work, f->geom, f->prec, rho, n, dirs, reproject, tc, cap);
+      lq_status st_run = stout_run_steps(f->ptr, e.work, f->geom, f->prec, rho, n, dirs, reproject, tc, cap, e.wfield);
       lq_status st_end = cuda_check(cudaStreamEndCapture(cap, &graph), "stout graph end capture");
       st = st_run != LQ_OK ? st_run : st_end;
     }
@@ -457,6 +590,7 @@ static lq_status run_graph(lq_field* f, double rho, int n, unsigned dirs, int re
     cudaStreamDestroy(cap);
     if (st != LQ_OK) {
       cudaFree(e.work);
+      if (e.wfield) cudaFree(e.wfield);
       return st;
     }
     it = graph_cache().emplace(k, e).first;
@@ -545,8 +679,9 @@ extern "C" lq_status lq_stout_smear(lq_field* links, double rho, int n_steps, un
     set_error("lq_stout_smear: opts->struct_size %d < sizeof(lq_stout_opts)", opts->struct_size);
     return LQ_ERR_ARG;
   }
-  if (o && (o->variant < 0 || o->variant > 2)) {
-    set_error("lq_stout_smear: variant %d is not available (0 tuned, 1 global, 2 shared memory)", o->variant);
+  if (o && (o->variant < 0 || o->variant > 3)) {
+    set_error("lq_stout_smear: variant %d is not available (0 tuned, 1 global, 2 shared memory, "
+              "3 two-link products)", o->variant);
     return LQ_ERR_UNSUPPORTED;
   }
   if (o && o->variant == 2 && links->prec != LQ_F32) {

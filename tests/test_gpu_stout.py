@@ -260,3 +260,37 @@ def test_reprojection(gpu, prec, scale):
     if scale == 1.0:
         plain = _run(U, prec, 0.1, 2, ALL, reproject=False).astype(np.complex128)
         assert np.max(np.abs(got - plain)) < (1e-6 if prec == lq.LQ_F32 else 1e-14)
+
+
+@pytest.mark.parametrize("dims,gen,rho,n,dirs", [
+    ((4, 4, 4, 4), "haar", 0.1, 1, ALL),
+    ((3, 4, 5, 6), "near", 0.125, 3, ALL),
+    ((3, 4, 5, 6), "near", 0.1, 2, SPATIAL),
+    ((5, 3, 2, 7), "haar", 0.25, 2, (1, 3)),
+    ((2, 2, 2, 2), "haar", 0.1, 2, ALL),
+    ((4, 4, 4, 4), "haar", 0.4, 2, ALL),
+])
+def test_two_link_product_variant(gpu, dims, gen, rho, n, dirs):
+    """Variant 3 (two-link products W_{mu nu}(y) = U_mu(y) U_nu(y+mu) formed
+    once per step, staples from them) against the oracle and against the
+    one-kernel step: the same staples with the products associated
+    differently, so equal to rounding."""
+    U = fieldgen.haar_su3(dims, 120) if gen == "haar" else fieldgen.near_identity_su3(dims, 120)
+    ref = stout.stout_smear(U, rho, n, dirs)
+    got = _run(U, lq.LQ_F64, rho, n, dirs, variant=3)
+    a, r = links_err(got, ref)
+    assert a <= F64_TOL and r <= F64_TOL, (a, r)
+    assert np.max(np.abs(got - _run(U, lq.LQ_F64, rho, n, dirs, variant=1))) <= 1e-14
+    got32 = _run(U, lq.LQ_F32, rho, n, dirs, variant=3)
+    assert np.max(np.abs(got32.astype(np.complex128) - ref)) <= F32_TOL_PER_STEP * n
+    for mu in range(4):
+        if mu not in dirs:
+            assert np.array_equal(got[..., mu, :, :], U[..., mu, :, :])
+
+
+def test_two_link_product_variant_in_graph(gpu):
+    dims = (4, 3, 4, 5)
+    U = fieldgen.near_identity_su3(dims, 121)
+    a = _run(U, lq.LQ_F64, 0.1, 3, ALL, variant=3, use_graph=True)
+    b = _run(U, lq.LQ_F64, 0.1, 3, ALL, variant=3)
+    assert np.array_equal(a, b)
