@@ -360,7 +360,7 @@ def main():
     # copies and transposes of each t-slab overlap the smearing of the others)
     pin_in = torch.from_numpy(U_host.astype(np.complex64).view(np.float32)).pin_memory()
     pin_out = torch.empty_like(pin_in).pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
 
     def e2e_step():
         return lq.stout_smear_host(pin_in, pin_out, g, lq.LQ_F32, RHO, N_SMEAR, DIRS, stream=stream)

@@ -220,11 +220,13 @@ static size_t wfield_bytes(const lq_geom& g, int prec, unsigned dirs) {
 template <typename R>
 __global__ void __launch_bounds__(128) k_wfield(const typename vec2<R>::type* __restrict__ U,
                                                 typename vec2<R>::type* __restrict__ W, GeomArgs g, PairMap pm) {
+  // the pairs of one site block run in consecutive CTAs, so their reads of
+  // the same links hit in L2 (a pair-major grid re-read the lattice per pair)
   const long long V = g.V;
-  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x % pm.n;
+  const long long sl = (long long)(blockIdx.x / pm.n) * blockDim.x + threadIdx.x;
   if (sl >= V) return;
   const int s = (int)sl;
-  const int p = blockIdx.y;
   const int mu = pm.mu[p], nu = pm.nu[p];
   int c[4];
   site_coords(g, s, c);
@@ -318,11 +320,11 @@ static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int
   const MuList ml = mu_list(dirs, &nd);
   if (tc.variant == 3 && wbuf) {
     const PairMap pm = pair_map(dirs);
-    const unsigned gs = (unsigned)((g.V + 127) / 128);
+    const unsigned gs = (unsigned)((g.V + 127) / 128 * pm.n);
     const int block = tc.block > 0 ? tc.block : 128;
     const dim3 grid((unsigned)(((g.V + block - 1) / block) * nd));
     if (prec == LQ_F64) {
-      k_wfield<double><<<dim3(gs, pm.n), 128, 0, s>>>((const double2*)in, (double2*)wbuf, g, pm);
+      k_wfield<double><<<gs, 128, 0, s>>>((const double2*)in, (double2*)wbuf, g, pm);
       if (reproject)
         k_stout_wf<double, true><<<grid, block, 0, s>>>((const double2*)in, (const double2*)wbuf, (double2*)out, g,
                                                         rho, dirs, nd, ml, pm);
@@ -330,7 +332,7 @@ static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int
         k_stout_wf<double, false><<<grid, block, 0, s>>>((const double2*)in, (const double2*)wbuf, (double2*)out, g,
                                                          rho, dirs, nd, ml, pm);
     } else {
-      k_wfield<float><<<dim3(gs, pm.n), 128, 0, s>>>((const float2*)in, (float2*)wbuf, g, pm);
+      k_wfield<float><<<gs, 128, 0, s>>>((const float2*)in, (float2*)wbuf, g, pm);
       if (reproject)
         k_stout_wf<float, true><<<grid, block, 0, s>>>((const float2*)in, (const float2*)wbuf, (float2*)out, g,
                                                        (float)rho, dirs, nd, ml, pm);
