@@ -160,13 +160,18 @@ def jacobi32(args, torch, lq, fieldgen):
             k = lq.LQ_COLOR_VECTOR if nspin == 1 else lq.LQ_FERMION
             chi = lq.Field(fU.geom, k, prec)
             chi.tensor.normal_()
-            t = _events(torch, lambda: lq.jacobi_smear(fU, chi, 0.21, n_iter, 1.0), args.steps, args.warmup)
             eb = 8 if prec == lq.LQ_F32 else 16
-            bytes_site = 4 * 9 * eb + 3 * 3 * nspin * eb
             flops = JACOBI_FLOPS_PER_SPIN * nspin * V * n_iter
-            res[kind] = {"ms": t, "gflops": flops / (t * 1e-3) / 1e9,
-                         "gb_s": bytes_site * V * n_iter / (t * 1e-3) / 1e9,
-                         "hbm_frac": bytes_site * V * n_iter / (t * 1e-3) / 1e9 / hbm}
+            for packed in (False, True):
+                t = _events(torch, lambda: lq.jacobi_smear(fU, chi, 0.21, n_iter, 1.0, compress_links=packed),
+                            args.steps, args.warmup)
+                # per iteration: each link (rows 0-1 only when packed) and chi, s0 read once, chi written;
+                # packing reads rows 0-1 and writes them once per call
+                bytes_site = 4 * (6 if packed else 9) * eb + 3 * 3 * nspin * eb
+                total = bytes_site * V * n_iter + (2 * 4 * 6 * eb * V if packed else 0)
+                res[kind + ("_compressed" if packed else "")] = {
+                    "ms": t, "gflops": flops / (t * 1e-3) / 1e9, "gb_s": total / (t * 1e-3) / 1e9,
+                    "hbm_frac": total / (t * 1e-3) / 1e9 / hbm}
         out[name] = res
     out["value"] = out["f32_32c64"]["vector"]["gflops"]
     out["dtype"] = "f32"

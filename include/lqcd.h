@@ -323,6 +323,21 @@ lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, in
 lq_status lq_jacobi_smear(const lq_field* links, lq_field* chi_inout, double kappa, int n_iter, double norm,
                           unsigned dirs_mask, void* stream);
 
+typedef struct lq_jacobi_opts {
+  int struct_size;        /* sizeof(lq_jacobi_opts); 0 => defaults                  */
+  int compress_links;     /* 1: the iterations read rows 0 and 1 of each link from a
+                             packed copy (made once per call, 2/3 of the link
+                             bytes) and rebuild row 2 = conj(row0 x row1); exact for
+                             SU(3) links, to rounding for links unitary to
+                             rounding; wrong for links outside SU(3).  0: off    */
+} lq_jacobi_opts;
+
+/* lq_jacobi_smear with options (opts NULL => lq_jacobi_smear).  Compressed
+ * links cut the HBM traffic of each iteration; the paper has no counterpart
+ * (its Sec. 8 names the memory layout as the next optimisation). */
+lq_status lq_jacobi_smear_ex(const lq_field* links, lq_field* chi_inout, double kappa, int n_iter, double norm,
+                             unsigned dirs_mask, const lq_jacobi_opts* opts, void* stream);
+
 /* exp(iQ) of every matrix of a COLOR_MATRIX field of Hermitian traceless Q,
  * through the same Cayley-Hamilton evaluation as the stout step ([MP]
  * Sec. III): coefficients f0, f1, f2 in FP64 from c0 = det Q and

@@ -317,10 +317,16 @@ def expiq(out, q, stream=None):
     _check(L.load().lq_expiq(out.handle, q.handle, _stream(stream)), "lq_expiq")
 
 
-def jacobi_smear(links, chi, kappa, n_iter, norm=1.0, dirs=(0, 1, 2, 3), stream=None):
-    """In-place Jacobi smearing of a COLOR_VECTOR or FERMION field (Listing 1)."""
-    _check(L.load().lq_jacobi_smear(links.handle, chi.handle, float(kappa), int(n_iter), float(norm),
-                                    dirs_mask(dirs), _stream(stream)), "lq_jacobi_smear")
+class LqJacobiOpts(ctypes.Structure):
+    _fields_ = [("struct_size", c_int), ("compress_links", c_int)]
+
+
+def jacobi_smear(links, chi, kappa, n_iter, norm=1.0, dirs=(0, 1, 2, 3), stream=None, compress_links=False):
+    """In-place Jacobi smearing of a COLOR_VECTOR or FERMION field (Listing 1); compress_links
+    reads rows 0-1 of each link and rebuilds row 2 (lq_jacobi_smear_ex)."""
+    o = LqJacobiOpts(ctypes.sizeof(LqJacobiOpts), int(bool(compress_links)))
+    _check(L.load().lq_jacobi_smear_ex(links.handle, chi.handle, float(kappa), int(n_iter), float(norm),
+                                       dirs_mask(dirs), byref(o), _stream(stream)), "lq_jacobi_smear")
 
 
 def stout_smear_batch(fields, rho, n_steps, dirs=(0, 1, 2), stream=None, **opts):

@@ -11,7 +11,40 @@
 
 namespace lq {
 
-template <typename R, int NSPIN>
+// A link from the full [dir][9][V] layout, or (PACKED) from rows 0 and 1 in a
+// [dir][6][V] copy with row 2 = conj(row 0 x row 1), exact for SU(3): 2/3 of
+// the link bytes of this HBM-bound kernel for 18 complex multiply-adds.
+template <typename R, bool PACKED>
+__device__ __forceinline__ M3<R> jacobi_link(const typename vec2<R>::type* __restrict__ U, long long V, int mu,
+                                             int s) {
+  if (!PACKED) return ld_link<R>(U, V, mu, s);
+  M3<R> m;
+  const typename vec2<R>::type* p = U + (long long)mu * 6 * V + s;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const typename vec2<R>::type e = __ldg(p + (long long)c * V);
+    m.e[c] = mkc<R>(e.x, e.y);
+  }
+  auto cross = [&](int a, int b, int c, int d) {
+    const cx<R> t = cmul(m.e[c], m.e[d]);
+    return cconj(cfma(m.e[a], m.e[b], mkc<R>(-t.re, -t.im)));
+  };
+  m.e[6] = cross(1, 5, 2, 4);
+  m.e[7] = cross(2, 3, 0, 5);
+  m.e[8] = cross(0, 4, 1, 3);
+  return m;
+}
+
+template <typename R>
+__global__ void k_pack12(const typename vec2<R>::type* __restrict__ U, typename vec2<R>::type* __restrict__ P,
+                         long long V) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // over 4 dirs x 6 comps x V
+  if (i >= 24 * V) return;
+  const long long s = i % V, dc = i / V, mu = dc / 6, c = dc % 6;
+  P[i] = U[(mu * 9 + c) * V + s];
+}
+
+template <typename R, int NSPIN, bool PACKED = false>
 __global__ void __launch_bounds__(128) k_jacobi(const typename vec2<R>::type* __restrict__ U,
                                                 const typename vec2<R>::type* __restrict__ chi,
                                                 const typename vec2<R>::type* __restrict__ s0,
@@ -36,7 +69,7 @@ __global__ void __launch_bounds__(128) k_jacobi(const typename vec2<R>::type* __
     const int s_b = nb_bwd(g, s, c[mu], mu);
     {
       // U_mu(x) chi(x+mu)
-      const M3<R> u = ld_link<R>(U, V, mu, s);
+      const M3<R> u = jacobi_link<R, PACKED>(U, V, mu, s);
 #pragma unroll
       for (int sp = 0; sp < NSPIN; ++sp) {
         cx<R> v[3];
@@ -53,7 +86,7 @@ __global__ void __launch_bounds__(128) k_jacobi(const typename vec2<R>::type* __
     }
     {
       // U_mu(x-mu)^dag chi(x-mu)
-      const M3<R> u = ld_link<R>(U, V, mu, s_b);
+      const M3<R> u = jacobi_link<R, PACKED>(U, V, mu, s_b);
 #pragma unroll
       for (int sp = 0; sp < NSPIN; ++sp) {
         cx<R> v[3];
@@ -93,16 +126,21 @@ __global__ void k_scale(typename vec2<R>::type* __restrict__ f, long long n, R s
 }
 
 template <typename R>
-static void launch_jacobi(int nspin, const void* U, const void* in, const void* s0, void* out, const GeomArgs& g,
-                          double kappa, double scale, unsigned dirs, cudaStream_t s) {
+static void launch_jacobi(int nspin, bool packed, const void* U, const void* in, const void* s0, void* out,
+                          const GeomArgs& g, double kappa, double scale, unsigned dirs, cudaStream_t s) {
   typedef typename vec2<R>::type V2;
   const unsigned grid = (unsigned)((g.V + 127) / 128);
-  if (nspin == 4)
-    k_jacobi<R, 4><<<grid, 128, 0, s>>>((const V2*)U, (const V2*)in, (const V2*)s0, (V2*)out, g, (R)kappa, (R)scale,
-                                        dirs);
-  else
-    k_jacobi<R, 1><<<grid, 128, 0, s>>>((const V2*)U, (const V2*)in, (const V2*)s0, (V2*)out, g, (R)kappa, (R)scale,
-                                        dirs);
+#define LQ_J(NS, PK)                                                                                     \
+  k_jacobi<R, NS, PK><<<grid, 128, 0, s>>>((const V2*)U, (const V2*)in, (const V2*)s0, (V2*)out, g, (R)kappa, \
+                                           (R)scale, dirs)
+  if (nspin == 4) {
+    if (packed) LQ_J(4, true);
+    else LQ_J(4, false);
+  } else {
+    if (packed) LQ_J(1, true);
+    else LQ_J(1, false);
+  }
+#undef LQ_J
 }
 
 }  // namespace lq
@@ -111,7 +149,19 @@ using namespace lq;
 
 extern "C" lq_status lq_jacobi_smear(const lq_field* links, lq_field* chi, double kappa, int n_iter, double norm,
                                      unsigned dirs_mask, void* stream) {
+  return lq_jacobi_smear_ex(links, chi, kappa, n_iter, norm, dirs_mask, nullptr, stream);
+}
+
+extern "C" lq_status lq_jacobi_smear_ex(const lq_field* links, lq_field* chi, double kappa, int n_iter,
+                                        double norm, unsigned dirs_mask, const lq_jacobi_opts* opts,
+                                        void* stream) {
   clear_error();
+  const lq_jacobi_opts* o = (opts && opts->struct_size >= (int)sizeof(lq_jacobi_opts)) ? opts : nullptr;
+  if (opts && !o && opts->struct_size != 0) {
+    set_error("lq_jacobi_smear: opts->struct_size %d < sizeof(lq_jacobi_opts)", opts->struct_size);
+    return LQ_ERR_ARG;
+  }
+  const bool packed = o && o->compress_links;
   lq_status st = check_links(links, "lq_jacobi_smear");
   if (st != LQ_OK) return st;
   if ((st = check_dirs(dirs_mask, "lq_jacobi_smear")) != LQ_OK) return st;
@@ -141,19 +191,34 @@ extern "C" lq_status lq_jacobi_smear(const lq_field* links, lq_field* chi, doubl
   }
   // chi stays s0 until the end; iterations ping-pong between two work buffers
   void* w[2] = {nullptr, nullptr};
+  void* pk = nullptr;
   if ((st = scratch_alloc(&w[0], chi->bytes, s, "lq_jacobi_smear"))) return st;
   if ((st = scratch_alloc(&w[1], chi->bytes, s, "lq_jacobi_smear"))) {
     scratch_free(w[0], s);
     return st;
+  }
+  const void* U = links->ptr;
+  if (packed) {   // rows 0 and 1 of every link, once for all iterations
+    st = scratch_alloc(&pk, links->bytes / 9 * 6, s, "lq_jacobi_smear packed links");
+    if (st == LQ_OK) {
+      const long long n = 24 * g.V;
+      const unsigned grid = (unsigned)((n + 255) / 256);
+      if (chi->prec == LQ_F64)
+        k_pack12<double><<<grid, 256, 0, s>>>((const double2*)links->ptr, (double2*)pk, g.V);
+      else
+        k_pack12<float><<<grid, 256, 0, s>>>((const float2*)links->ptr, (float2*)pk, g.V);
+      st = launch_check("lq_jacobi_smear pack");
+      U = pk;
+    }
   }
   const void* cur = chi->ptr;
   for (int it = 0; it < n_iter && st == LQ_OK; ++it) {
     void* out = w[it & 1];
     const double scale = (it == n_iter - 1) ? 1.0 / norm : 1.0;
     if (chi->prec == LQ_F64)
-      launch_jacobi<double>(nspin, links->ptr, cur, chi->ptr, out, g, kappa, scale, dirs_mask, s);
+      launch_jacobi<double>(nspin, packed, U, cur, chi->ptr, out, g, kappa, scale, dirs_mask, s);
     else
-      launch_jacobi<float>(nspin, links->ptr, cur, chi->ptr, out, g, kappa, scale, dirs_mask, s);
+      launch_jacobi<float>(nspin, packed, U, cur, chi->ptr, out, g, kappa, scale, dirs_mask, s);
     st = launch_check("lq_jacobi_smear kernel");
     cur = out;
   }
@@ -161,5 +226,6 @@ extern "C" lq_status lq_jacobi_smear(const lq_field* links, lq_field* chi, doubl
     st = cuda_check(cudaMemcpyAsync(chi->ptr, cur, chi->bytes, cudaMemcpyDeviceToDevice, s), "lq_jacobi_smear copy");
   scratch_free(w[0], s);
   scratch_free(w[1], s);
+  if (pk) scratch_free(pk, s);
   return st;
 }

@@ -42,3 +42,26 @@ def test_jacobi_rejects_bad_arguments(gpu):
         with pytest.raises(lq.LqError) as e:
             lq.jacobi_smear(*args)
         assert e.value.status == status
+
+
+@pytest.mark.parametrize("kind", ["vector", "fermion"])
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+@pytest.mark.parametrize("dims,n_iter,dirs", [((4, 4, 4, 8), 5, (0, 1, 2, 3)), ((3, 5, 2, 7), 3, (0, 1, 2)),
+                                              ((2, 2, 2, 2), 2, (0, 1, 2, 3))])
+def test_jacobi_compressed_links(gpu, kind, prec, dims, n_iter, dirs):
+    """Links read as rows 0 and 1 with row 2 rebuilt as conj(row0 x row1):
+    exact for SU(3), so the result meets the oracle at the same tolerance."""
+    U = fieldgen.haar_su3(dims, 610)
+    v = fieldgen.color_vector(dims, 611)
+    chi = v if kind == "vector" else np.stack([v, 0.5 * v[::-1], 1j * v, -v], axis=-2)
+    ref = expr.jacobi_smear(U, chi, 0.21, n_iter, 1.7, dirs)
+    fU = upload_links(U, prec)
+    k = lq.LQ_COLOR_VECTOR if kind == "vector" else lq.LQ_FERMION
+    fchi = lq.Field.from_host(fU.geom, k, prec, chi)
+    lq.jacobi_smear(fU, fchi, 0.21, n_iter, 1.7, dirs, compress_links=True)
+    got = fchi.download().astype(np.complex128)
+    tol = 1e-12 if prec == lq.LQ_F64 else 1e-5 * max(1, n_iter)
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    plain = lq.Field.from_host(fU.geom, k, prec, chi)
+    lq.jacobi_smear(fU, plain, 0.21, n_iter, 1.7, dirs)
+    assert np.max(np.abs(got - plain.download().astype(np.complex128))) <= tol * np.max(np.abs(ref))
