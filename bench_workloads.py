@@ -16,6 +16,8 @@
                 expression micro-suite on the same field: sum_mu tr(U_mu(x)
                 U_mu(x+mu)), U_mu(x) U_nu(x+mu)^dag, plaquette; the two
                 programs interpreted and NVRTC-compiled.
+* ape48      -- 48^3 x 96, 6 APE steps alpha = 0.5 in 4 dims, FP32 (FP64
+                projection) and FP64.
 Inputs are resident on the device before timing; times are CUDA events.
 """
 import json
@@ -178,6 +180,39 @@ def jacobi32(args, torch, lq, fieldgen):
     return out
 
 
+# FP64 flops per link of the APE projection, counted from csrc/ape.cu: A = V^dag V 108,
+# eigenvalues and divided differences ~105, A^2 198, X 60, W = V X 198, det V 60,
+# phase sincos 38, W * phase 54 (the 5 square roots, ~5 divisions and the atan2
+# library calls are not counted); mixing 36 and the staple sum 2484 in the field precision.
+APE_PROJECTION_FLOPS = 108 + 105 + 198 + 60 + 198 + 60 + 38 + 54
+APE_MIX_FLOPS = 2484 + 36
+
+
+def ape48(args, torch, lq, fieldgen):
+    import bench
+    dims, n, alpha = (48, 48, 48, 96), 6, 0.5
+    V = int(np.prod(dims))
+    links = n * V * 4
+    out = {"metric": "APE link-updates/s", "unit": "link-updates/s",
+           "config": {"workload": "48^3x96, exp(i*0.3*H) links seed 2, 6 APE steps alpha=0.5 in 4 dims"}}
+    mhz = 2070.0
+    p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
+    for name, prec in (("f32", lq.LQ_F32), ("f64", lq.LQ_F64)):
+        f, _ = _field(lq, fieldgen, dims, 2, prec)
+        t = _events(torch, lambda: lq.ape_smear(f, alpha, n, (0, 1, 2, 3)), args.steps, args.warmup)
+        f64_flops = APE_PROJECTION_FLOPS + (APE_MIX_FLOPS if prec == lq.LQ_F64 else 0)
+        out[name] = {"ms": t, "value": links / (t * 1e-3),
+                     "roofline": {"bound": "alu", "pipe": "fp64", "fp64_flops_per_link": f64_flops,
+                                  "achieved": f64_flops * links / (t * 1e-3) / 1e12, "peak": p64 / 1e12,
+                                  "frac": f64_flops * links / (t * 1e-3) / p64, "unit": "TFLOP/s",
+                                  "note": "square roots, divisions and atan2 not counted"}}
+        del f
+        torch.cuda.empty_cache()
+    out["value"] = out["f32"]["value"]
+    out["dtype"] = "f32"
+    return out
+
+
 def micro16(args, torch, lq, fieldgen):
     dims = (16, 16, 16, 32)
     V = int(np.prod(dims))
@@ -217,7 +252,8 @@ def run(args):
     import fieldgen
     import paper_1105_2279_gb300 as lq
     torch.cuda.set_device(0)
-    fn = {"batch64": batch64, "backward24": backward24, "micro16": micro16, "jacobi32": jacobi32}[args.workload]
+    fn = {"batch64": batch64, "backward24": backward24, "micro16": micro16, "jacobi32": jacobi32,
+          "ape48": ape48}[args.workload]
     res = fn(args, torch, lq, fieldgen)
     res.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                 "data": "synthetic", "workload_mode": args.workload})

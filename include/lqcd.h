@@ -306,6 +306,17 @@ lq_status lq_stout_backward(const lq_field* thin_links, double rho, int n_steps,
 lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, int n_steps,
                                unsigned dirs_mask, const lq_stout_opts* opts, void* stream);
 
+/* APE smearing (Albanese et al., Phys. Lett. B 192 (1987) 163; the paper
+ * has no counterpart: an adjacent smearing on the stout step's staple sum),
+ * n_steps steps in place on a LINKS field:
+ *   V_mu(x) = (1 - alpha) U_mu(x) + alpha / (2 (d - 1)) * C_mu(x),  d = |dirs|,
+ *   U'_mu(x) = W exp(-i arg(det W) / 3),  W = V (V^dag V)^(-1/2)  (polar factor),
+ * C_mu the staple sum of lq_stout_smear (without rho), arg in (-pi, pi].
+ * The mixing runs in the field precision, the projection in FP64.  V must
+ * be non-singular (a singular V gives NaN).  alpha finite; n_steps >= 0;
+ * dirs_mask in [1, 15]; links outside dirs are unchanged. */
+lq_status lq_ape_smear(lq_field* links_inout, double alpha, int n_steps, unsigned dirs_mask, void* stream);
+
 /* ---- Jacobi smearing ([W] Sec. 6, Listing 1 and the operator K) ----------- */
 
 /* n_iter Jacobi smearing iterations of a quark field, in place:

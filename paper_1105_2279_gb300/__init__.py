@@ -317,6 +317,12 @@ def expiq(out, q, stream=None):
     _check(L.load().lq_expiq(out.handle, q.handle, _stream(stream)), "lq_expiq")
 
 
+def ape_smear(links, alpha, n_steps, dirs=(0, 1, 2, 3), stream=None):
+    """In-place APE smearing of a LINKS field (lq_ape_smear)."""
+    _check(L.load().lq_ape_smear(links.handle, float(alpha), int(n_steps), dirs_mask(dirs), _stream(stream)),
+           "lq_ape_smear")
+
+
 class LqJacobiOpts(ctypes.Structure):
     _fields_ = [("struct_size", c_int), ("compress_links", c_int)]
 
