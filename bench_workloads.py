@@ -181,10 +181,11 @@ def jacobi32(args, torch, lq, fieldgen):
 
 
 # FP64 flops per link of the APE projection, counted from csrc/ape.cu: A = V^dag V 108,
-# eigenvalues and divided differences ~105, A^2 198, X 60, W = V X 198, det V 60,
-# phase sincos 38, W * phase 54 (the 5 square roots, ~5 divisions and the atan2
-# library calls are not counted); mixing 36 and the staple sum 2484 in the field precision.
-APE_PROJECTION_FLOPS = 108 + 105 + 198 + 60 + 198 + 60 + 38 + 54
+# eigenvalues and divided differences ~105, A^2 (Hermitian, compact) 40, X 30,
+# W = V X 198, det V 60, cube root of the determinant phase ~40, W * phase 54 (the
+# Newton refinements of 7 inverse square roots and 2 reciprocals are not counted);
+# mixing 36 and the staple sum 2484 in the field precision.
+APE_PROJECTION_FLOPS = 108 + 105 + 40 + 30 + 198 + 60 + 40 + 54
 APE_MIX_FLOPS = 2484 + 36
 
 
@@ -205,7 +206,7 @@ def ape48(args, torch, lq, fieldgen):
                      "roofline": {"bound": "alu", "pipe": "fp64", "fp64_flops_per_link": f64_flops,
                                   "achieved": f64_flops * links / (t * 1e-3) / 1e12, "peak": p64 / 1e12,
                                   "frac": f64_flops * links / (t * 1e-3) / p64, "unit": "TFLOP/s",
-                                  "note": "square roots, divisions and atan2 not counted"}}
+                                  "note": "Newton refinements of square roots and reciprocals not counted"}}
         del f
         torch.cuda.empty_cache()
     out["value"] = out["f32"]["value"]
