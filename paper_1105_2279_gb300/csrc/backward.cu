@@ -112,7 +112,7 @@ __device__ __forceinline__ M3<R> ld(const V2<R>* __restrict__ F, long long V, in
 //                 + U_mu(y-mu)^dag U_a(y-mu) K_mu(y-mu+a)
 //                 + U_mu(y-mu)^dag K_a(y-mu) U_mu(y-mu+a) + U_mu(y) K_a(y+mu) U_mu(y+a)^dag ]
 template <typename R>
-__global__ void __launch_bounds__(128) k_bwd_staple(const V2<R>* __restrict__ U, const V2<R>* __restrict__ K,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_bwd_staple(const V2<R>* __restrict__ U, const V2<R>* __restrict__ K,
                                                     V2<R>* __restrict__ G, GeomArgs g, unsigned dirs) {
   const long long V = g.V;
   const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
