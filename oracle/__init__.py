@@ -30,6 +30,9 @@ operations (``np.roll`` for shifts, ``@`` for 3x3 products):
 * ``ape``      -- APE link smearing (Albanese et al., Phys. Lett. B 192
   (1987) 163): links mixed with their staples, projected back to SU(3) by
   the unitary polar factor with the determinant phase removed.
+* ``hyp``      -- HYP smearing (Hasenfratz and Knechtli, Phys. Rev. D 64
+  (2001) 034504): three nested APE-type levels with staples confined to the
+  hypercubes attached to the link.
 
 Field convention: a link field is an array of shape (Lt, Lz, Ly, Lx, 4, 3, 3)
 complex128, i.e. site-major with x fastest, direction mu = 0,1,2,3 = x,y,z,t,
