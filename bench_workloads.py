@@ -18,6 +18,8 @@
                 programs interpreted and NVRTC-compiled.
 * ape48      -- 48^3 x 96, 6 APE steps alpha = 0.5 in 4 dims, FP32 (FP64
                 projection) and FP64.
+* hyp32      -- 32^3 x 64, 2 HYP steps (0.75, 0.6, 0.3), FP32 (FP64
+                projections) and FP64.
 Inputs are resident on the device before timing; times are CUDA events.
 """
 import json
@@ -214,6 +216,40 @@ def ape48(args, torch, lq, fieldgen):
     return out
 
 
+# HYP per site and step: level 3 12 links x (4 products + mixing 36), level 2
+# 12 x (8 + 36), level 1 4 x (12 + 36) in the field precision (38.4 k flops),
+# and 28 FP64 projections.
+HYP_MIX_FLOPS_PER_SITE = 12 * (4 * 198 + 36) + 12 * (8 * 198 + 36) + 4 * (12 * 198 + 36)
+HYP_PROJECTIONS_PER_SITE = 28
+
+
+def hyp32(args, torch, lq, fieldgen):
+    import bench
+    dims, n = (32, 32, 32, 64), 2
+    V = int(np.prod(dims))
+    links = n * V * 4
+    out = {"metric": "HYP link-updates/s", "unit": "link-updates/s",
+           "config": {"workload": "32^3x64, exp(i*0.3*H) links seed 2, 2 HYP steps (0.75, 0.6, 0.3)"}}
+    mhz = 2070.0
+    p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
+    for name, prec in (("f32", lq.LQ_F32), ("f64", lq.LQ_F64)):
+        f, _ = _field(lq, fieldgen, dims, 2, prec)
+        t = _events(torch, lambda: lq.hyp_smear(f, 0.75, 0.6, 0.3, n), args.steps, args.warmup)
+        f64_site = HYP_PROJECTIONS_PER_SITE * APE_PROJECTION_FLOPS + (HYP_MIX_FLOPS_PER_SITE if prec == lq.LQ_F64
+                                                                      else 0)
+        ach = f64_site * V * n / (t * 1e-3)
+        out[name] = {"ms": t, "value": links / (t * 1e-3),
+                     "roofline": {"bound": "alu", "pipe": "fp64", "fp64_flops_per_link": f64_site / 4,
+                                  "achieved": ach / 1e12, "peak": p64 / 1e12, "frac": ach / p64,
+                                  "unit": "TFLOP/s",
+                                  "note": "Newton refinements of square roots and reciprocals not counted"}}
+        del f
+        torch.cuda.empty_cache()
+    out["value"] = out["f32"]["value"]
+    out["dtype"] = "f32"
+    return out
+
+
 def micro16(args, torch, lq, fieldgen):
     dims = (16, 16, 16, 32)
     V = int(np.prod(dims))
@@ -254,7 +290,7 @@ def run(args):
     import paper_1105_2279_gb300 as lq
     torch.cuda.set_device(0)
     fn = {"batch64": batch64, "backward24": backward24, "micro16": micro16, "jacobi32": jacobi32,
-          "ape48": ape48}[args.workload]
+          "ape48": ape48, "hyp32": hyp32}[args.workload]
     res = fn(args, torch, lq, fieldgen)
     res.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                 "data": "synthetic", "workload_mode": args.workload})

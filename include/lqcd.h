@@ -317,6 +317,16 @@ lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, in
  * dirs_mask in [1, 15]; links outside dirs are unchanged. */
 lq_status lq_ape_smear(lq_field* links_inout, double alpha, int n_steps, unsigned dirs_mask, void* stream);
 
+/* HYP smearing (Hasenfratz and Knechtli, Phys. Rev. D 64 (2001) 034504; the
+ * paper has no counterpart), n_steps steps in place on a LINKS field, all
+ * four directions: three nested APE-type levels with weights a3 (innermost,
+ * 2 staples), a2 (4 staples) and a1 (outermost, 6 staples), whose staples
+ * stay inside the hypercubes attached to the link, each level projected to
+ * SU(3) as in lq_ape_smear; usual weights (a1, a2, a3) = (0.75, 0.6, 0.3).
+ * Staples and mixing in the field precision, projections in FP64.  Scratch:
+ * 24 colour-matrix fields of decorated links and one link field. */
+lq_status lq_hyp_smear(lq_field* links_inout, double a1, double a2, double a3, int n_steps, void* stream);
+
 /* ---- Jacobi smearing ([W] Sec. 6, Listing 1 and the operator K) ----------- */
 
 /* n_iter Jacobi smearing iterations of a quark field, in place:

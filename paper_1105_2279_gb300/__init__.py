@@ -323,6 +323,12 @@ def ape_smear(links, alpha, n_steps, dirs=(0, 1, 2, 3), stream=None):
            "lq_ape_smear")
 
 
+def hyp_smear(links, a1=0.75, a2=0.6, a3=0.3, n_steps=1, stream=None):
+    """In-place HYP smearing of a LINKS field, all four directions (lq_hyp_smear)."""
+    _check(L.load().lq_hyp_smear(links.handle, float(a1), float(a2), float(a3), int(n_steps), _stream(stream)),
+           "lq_hyp_smear")
+
+
 class LqJacobiOpts(ctypes.Structure):
     _fields_ = [("struct_size", c_int), ("compress_links", c_int)]
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "lq_jacobi_smear": (c_int, [_P, _P, c_double, c_int, c_double, c_uint, _P]),
     "lq_jacobi_smear_ex": (c_int, [_P, _P, c_double, c_int, c_double, c_uint, _P, _P]),
     "lq_ape_smear": (c_int, [_P, c_double, c_int, c_uint, _P]),
+    "lq_hyp_smear": (c_int, [_P, c_double, c_double, c_double, c_int, _P]),
     "lq_expiq": (c_int, [_P, _P, _P]),
     "lq_stout_ch_stats": (c_int, [_P, c_double, c_int, c_uint, _P, _P]),
     "lq_stout_smear_host": (c_int, [_P, _P, _P, c_int, c_double, c_int, c_uint, c_int, _P, _P, _P]),
