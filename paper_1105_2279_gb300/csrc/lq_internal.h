@@ -104,6 +104,16 @@ TuneChoice stout_default_choice(int prec);
 lq_status stout_step_range(const void* in, void* out, const lq_geom& g, int prec, double rho, unsigned dirs,
                            int reproject, const TuneChoice& tc, long long s_begin, long long s_end,
                            cudaStream_t s);
+// Independent site ranges, each with its own input and output field, in one
+// launch per kMaxSegs ranges (the same per-link arithmetic as lq_stout_smear).
+constexpr int kMaxSegs = 8;
+struct StepSegment {
+  const void* in;
+  void* out;
+  long long s_begin, s_end;
+};
+lq_status stout_step_segments(const StepSegment* seg, int nseg, const lq_geom& g, int prec, double rho,
+                              unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s);
 // AoS <-> SoA transpose of the sites [s_begin, s_end) of a field of this kind,
 // between a whole-lattice AoS buffer and a whole-lattice SoA buffer.
 lq_status transpose_range(const void* src, void* dst, const lq_geom& g, int kind, int prec, bool to_soa,

@@ -41,9 +41,10 @@ template <typename R, bool REPRO, bool COUNT>
 __device__ __forceinline__ void stout_global_body(const typename vec2<R>::type* __restrict__ Uin,
                                                   typename vec2<R>::type* __restrict__ Uout, const GeomArgs& g,
                                                   R rho, unsigned dirs, int nsite, int nd, const MuList& ml,
-                                                  unsigned long long* stats, int s_begin, int s_end) {
-  const int mi = blockIdx.x % nd;
-  const long long sb = blockIdx.x / nd;
+                                                  unsigned long long* stats, int s_begin, int s_end,
+                                                  int blk) {
+  const int mi = blk % nd;
+  const long long sb = blk / nd;
   const int mu = mi == 0 ? ml.mu[0] : (mi == 1 ? ml.mu[1] : (mi == 2 ? ml.mu[2] : ml.mu[3]));
   const long long V = g.V;
   for (int k = 0; k < nsite; ++k) {
@@ -66,7 +67,7 @@ template <bool REPRO, bool COUNT = false>
 __global__ void __maxnreg__(72) k_stout_global_f32(const float2* __restrict__ Uin, float2* __restrict__ Uout,
                                                    GeomArgs g, float rho, unsigned dirs, int nsite, int nd,
                                                    MuList ml, unsigned long long* stats, int s_begin, int s_end) {
-  stout_global_body<float, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats, s_begin, s_end);
+  stout_global_body<float, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats, s_begin, s_end, blockIdx.x);
 }
 
 template <bool REPRO, bool COUNT = false>
@@ -74,7 +75,42 @@ __global__ void __launch_bounds__(256) k_stout_global_f64(const double2* __restr
                                                           double2* __restrict__ Uout, GeomArgs g, double rho,
                                                           unsigned dirs, int nsite, int nd, MuList ml,
                                                           unsigned long long* stats, int s_begin, int s_end) {
-  stout_global_body<double, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats, s_begin, s_end);
+  stout_global_body<double, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats, s_begin, s_end,
+                                          blockIdx.x);
+}
+
+// Several independent site ranges, each with its own input and output field,
+// in one launch (the host-streamed path runs the (step, slab) items of one
+// wavefront key together: one grid tail instead of one per slab).
+struct SegList {
+  const void* in[kMaxSegs];
+  void* out[kMaxSegs];
+  int s0[kMaxSegs], s1[kMaxSegs];
+  int bstart[kMaxSegs + 1];   // first block of each segment; bstart[n] = grid size
+  int n;
+};
+
+template <typename R, bool REPRO>
+__device__ __forceinline__ void stout_seg_body(const SegList& sg, GeomArgs g, R rho, unsigned dirs, int nsite,
+                                               int nd, MuList ml) {
+  int j = 0;
+#pragma unroll 1
+  while (j + 1 < sg.n && (int)blockIdx.x >= sg.bstart[j + 1]) ++j;
+  typedef typename vec2<R>::type V2;
+  stout_global_body<R, REPRO, false>((const V2*)sg.in[j], (V2*)sg.out[j], g, rho, dirs, nsite, nd, ml, nullptr,
+                                     sg.s0[j], sg.s1[j], (int)blockIdx.x - sg.bstart[j]);
+}
+
+template <bool REPRO>
+__global__ void __maxnreg__(72) k_stout_seg_f32(SegList sg, GeomArgs g, float rho, unsigned dirs, int nsite, int nd,
+                                                MuList ml) {
+  stout_seg_body<float, REPRO>(sg, g, rho, dirs, nsite, nd, ml);
+}
+
+template <bool REPRO>
+__global__ void __launch_bounds__(256) k_stout_seg_f64(SegList sg, GeomArgs g, double rho, unsigned dirs, int nsite,
+                                                       int nd, MuList ml) {
+  stout_seg_body<double, REPRO>(sg, g, rho, dirs, nsite, nd, ml);
 }
 
 // Variant 2 (FP32): shared-memory staging.  A CTA owns a BX x BY x BZ block of
@@ -310,6 +346,45 @@ lq_status stout_step_range(const void* in, void* out, const lq_geom& geom, int p
   TuneChoice t = tc;
   if (t.variant != 1) t = stout_default_choice(prec);   // variants 2 and 3 work on whole lattices
   return launch_global(in, out, geom_args(geom), prec, rho, dirs, reproject, t, s_begin, s_end, s);
+}
+
+lq_status stout_step_segments(const StepSegment* seg, int nseg, const lq_geom& geom, int prec, double rho,
+                              unsigned dirs, int reproject, const TuneChoice& tc, cudaStream_t s) {
+  TuneChoice t = tc;
+  if (t.variant != 1) t = stout_default_choice(prec);
+  const GeomArgs g = geom_args(geom);
+  int nd = 0;
+  const MuList ml = mu_list(dirs, &nd);
+  const int block = t.block > 0 ? t.block : 128;
+  const int nsite = t.nsite > 0 ? t.nsite : 1;
+  const long long per_block = (long long)block * nsite;
+  for (int first = 0; first < nseg; first += kMaxSegs) {
+    SegList sl;
+    sl.n = nseg - first < kMaxSegs ? nseg - first : kMaxSegs;
+    long long b = 0;
+    for (int j = 0; j < sl.n; ++j) {
+      const StepSegment& e = seg[first + j];
+      sl.in[j] = e.in;
+      sl.out[j] = e.out;
+      sl.s0[j] = (int)e.s_begin;
+      sl.s1[j] = (int)e.s_end;
+      sl.bstart[j] = (int)b;
+      b += ((e.s_end - e.s_begin + per_block - 1) / per_block) * nd;
+    }
+    sl.bstart[sl.n] = (int)b;
+    for (int j = sl.n + 1; j <= kMaxSegs; ++j) sl.bstart[j] = (int)b;
+    if (b == 0) continue;
+    if (prec == LQ_F64) {
+      if (reproject) k_stout_seg_f64<true><<<(unsigned)b, block, 0, s>>>(sl, g, rho, dirs, nsite, nd, ml);
+      else k_stout_seg_f64<false><<<(unsigned)b, block, 0, s>>>(sl, g, rho, dirs, nsite, nd, ml);
+    } else {
+      if (reproject) k_stout_seg_f32<true><<<(unsigned)b, block, 0, s>>>(sl, g, (float)rho, dirs, nsite, nd, ml);
+      else k_stout_seg_f32<false><<<(unsigned)b, block, 0, s>>>(sl, g, (float)rho, dirs, nsite, nd, ml);
+    }
+    lq_status st = launch_check("stout step kernel (segments)");
+    if (st != LQ_OK) return st;
+  }
+  return LQ_OK;
 }
 
 static lq_status launch_step(const void* in, void* out, const lq_geom& geom, int prec, double rho,

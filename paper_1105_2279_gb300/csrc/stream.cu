@@ -77,6 +77,7 @@ struct Trace {
     char what[12];
     int slab, step;
     cudaEvent_t a, b;
+    bool owns;
   };
   std::vector<Op> ops;
   Trace() {
@@ -96,9 +97,20 @@ struct Trace {
     o.step = step;
     cudaEventCreate(&o.a);
     cudaEventCreate(&o.b);
+    o.owns = true;
     cudaEventRecord(o.a, s);
     ops.push_back(o);
     return (int)ops.size() - 1;
+  }
+  // another operation that ran inside the same launch as op `id`
+  void alias(const char* what, int slab, int step, int id) {
+    if (id < 0) return;
+    Op o = ops[id];
+    snprintf(o.what, sizeof(o.what), "%s", what);
+    o.slab = slab;
+    o.step = step;
+    o.owns = false;
+    ops.push_back(o);
   }
   void close(int id, cudaStream_t s) {
     if (id >= 0) cudaEventRecord(ops[id].b, s);
@@ -117,10 +129,11 @@ struct Trace {
     }
   }
   ~Trace() {
-    for (Op& o : ops) {
-      cudaEventDestroy(o.a);
-      cudaEventDestroy(o.b);
-    }
+    for (Op& o : ops)
+      if (o.owns) {
+        cudaEventDestroy(o.a);
+        cudaEventDestroy(o.b);
+      }
     if (t0) cudaEventDestroy(t0);
   }
 };
@@ -250,22 +263,40 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
       if (st == LQ_OK) st = cuda_check(cudaEventRecord(fin[i], s), "pipeline final event");
       done_order.push_back(i);
     }
-  for (const Item& it : items) {
-    if (st != LQ_OK) break;
-    const int k = it.k, i = it.i;
-    if (k == 1) {
-      const int nb[3] = {(i + nc - 1) % nc, i, (i + 1) % nc};
-      for (int j : nb)
-        if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(s, up[j], 0), "pipeline wait");
+  // items of one wavefront key are independent: they run as one launch of the
+  // multi-segment step kernel (one grid tail per key instead of per slab)
+  for (size_t a = 0; a < items.size() && st == LQ_OK;) {
+    if (items[a].i < 0) {   // whole-lattice step
+      const int k = items[a].k;
+      const int t = tr.open("step", -1, k, s);
+      st = stout_step_range(f[(k - 1) % 2], f[k % 2], g, prec, rho, dirs_mask, reproject, tc, 0, V, s);
+      tr.close(t, s);
+      ++a;
+      continue;
     }
-    const int t = tr.open("step", i, k, s);
-    const long long s0 = i < 0 ? 0 : sb[i], s1 = i < 0 ? V : sb[i + 1];
-    if (st == LQ_OK) st = stout_step_range(f[(k - 1) % 2], f[k % 2], g, prec, rho, dirs_mask, reproject, tc, s0, s1, s);
-    tr.close(t, s);
-    if (st == LQ_OK && k == n_steps) {
-      st = cuda_check(cudaEventRecord(fin[i], s), "pipeline final event");
-      done_order.push_back(i);
+    size_t b = a;
+    while (b < items.size() && items[b].i >= 0 && items[b].key == items[a].key) ++b;
+    std::vector<StepSegment> segs;
+    for (size_t t = a; t < b && st == LQ_OK; ++t) {
+      const int k = items[t].k, i = items[t].i;
+      if (k == 1) {
+        const int nb[3] = {(i + nc - 1) % nc, i, (i + 1) % nc};
+        for (int j : nb)
+          if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(s, up[j], 0), "pipeline wait");
+      }
+      segs.push_back({f[(k - 1) % 2], f[k % 2], sb[i], sb[i + 1]});
     }
+    const int t0 = tr.open("step", items[a].i, items[a].k, s);
+    if (st == LQ_OK)
+      st = stout_step_segments(segs.data(), (int)segs.size(), g, prec, rho, dirs_mask, reproject, tc, s);
+    tr.close(t0, s);
+    for (size_t t = a + 1; t < b; ++t) tr.alias("step", items[t].i, items[t].k, t0);
+    for (size_t t = a; t < b && st == LQ_OK; ++t)
+      if (items[t].k == n_steps) {
+        st = cuda_check(cudaEventRecord(fin[items[t].i], s), "pipeline final event");
+        done_order.push_back(items[t].i);
+      }
+    a = b;
   }
   void* result = f[n_steps % 2];
   for (int i : done_order) {
