@@ -30,6 +30,10 @@ operations (``np.roll`` for shifts, ``@`` for 3x3 products):
 * ``ape``      -- APE link smearing (Albanese et al., Phys. Lett. B 192
   (1987) 163): links mixed with their staples, projected back to SU(3) by
   the unitary polar factor with the determinant phase removed.
+* ``ape_force`` -- reverse-mode gradient through APE steps: the SU(3)
+  projection's gradient from Jacobi's determinant formula and the
+  Daleckii-Krein formula for the Frechet derivative of A^(-1/2), and the
+  staple sum's from ``backward``.
 * ``hyp``      -- HYP smearing (Hasenfratz and Knechtli, Phys. Rev. D 64
   (2001) 034504): three nested APE-type levels with staples confined to the
   hypercubes attached to the link.

@@ -21,6 +21,30 @@ from .stout import staple_sum, stout_smear_steps
 from .su3 import adj, ta
 
 
+def staple_vjp(U, mu, dirs, K, G):
+    """Adds to G the gradient through the bare staple sum S_mu of ``staple_sum``,
+    given K = G_S (the gradient w.r.t. S_mu at every site)."""
+    Umu = U[..., mu, :, :]
+    for nu in dirs:
+        if nu == mu:
+            continue
+        Unu = U[..., nu, :, :]
+        # upper staple A = P Qm R^dag, P = U_nu(x), Qm = U_mu(x+nu), R = U_nu(x+mu)
+        P = Unu
+        Qm = shift(Umu, nu, +1)
+        R = shift(Unu, mu, +1)
+        G[..., nu, :, :] += K @ R @ adj(Qm)
+        G[..., mu, :, :] += shift(adj(P) @ K @ R, nu, -1)
+        G[..., nu, :, :] += shift(adj(K) @ P @ Qm, mu, -1)
+        # lower staple B = P^dag Qm R, P = U_nu(x-nu), Qm = U_mu(x-nu), R = U_nu(x-nu+mu)
+        P = shift(Unu, nu, -1)
+        Qm = shift(Umu, nu, -1)
+        R = shift(shift(Unu, mu, +1), nu, -1)
+        G[..., nu, :, :] += shift(Qm @ R @ adj(K), nu, +1)
+        G[..., mu, :, :] += shift(P @ K @ adj(R), nu, +1)
+        G[..., nu, :, :] += shift(shift(adj(Qm) @ P @ K, nu, +1), mu, -1)
+
+
 def stout_step_vjp(U, rho, dirs, Gp):
     """Gradient w.r.t. the step input U, given Gp = gradient w.r.t. the step output."""
     G = Gp.copy()                       # links outside `dirs` pass through unchanged
@@ -38,25 +62,7 @@ def stout_step_vjp(U, rho, dirs, Gp):
         # E = exp(X); X = TA(Omega); Omega = C U^dag
         G_Om = ta(expm_frechet(adj(X), G_E))
         G[..., mu, :, :] += adj(G_Om) @ C          # via U^dag in Omega
-        K = rho * (G_Om @ Umu)                     # gradient w.r.t. the bare staple sum
-        for nu in dirs:
-            if nu == mu:
-                continue
-            Unu = U[..., nu, :, :]
-            # upper staple A = P Qm R^dag, P = U_nu(x), Qm = U_mu(x+nu), R = U_nu(x+mu)
-            P = Unu
-            Qm = shift(Umu, nu, +1)
-            R = shift(Unu, mu, +1)
-            G[..., nu, :, :] += K @ R @ adj(Qm)
-            G[..., mu, :, :] += shift(adj(P) @ K @ R, nu, -1)
-            G[..., nu, :, :] += shift(adj(K) @ P @ Qm, mu, -1)
-            # lower staple B = P^dag Qm R, P = U_nu(x-nu), Qm = U_mu(x-nu), R = U_nu(x-nu+mu)
-            P = shift(Unu, nu, -1)
-            Qm = shift(Umu, nu, -1)
-            R = shift(shift(Unu, mu, +1), nu, -1)
-            G[..., nu, :, :] += shift(Qm @ R @ adj(K), nu, +1)
-            G[..., mu, :, :] += shift(P @ K @ adj(R), nu, +1)
-            G[..., nu, :, :] += shift(shift(adj(Qm) @ P @ K, nu, +1), mu, -1)
+        staple_vjp(U, mu, dirs, rho * (G_Om @ Umu), G)   # K: gradient w.r.t. the bare staple sum
     return G
 
 
