@@ -20,6 +20,10 @@
                 projection) and FP64.
 * hyp32      -- 32^3 x 64, 2 HYP steps (0.75, 0.6, 0.3), FP32 (FP64
                 projections) and FP64.
+* apeforce24 -- 24^3 x 48, 3 APE steps alpha = 0.6 in 4 dims, gradient of the
+                Wilson action (beta = 6) of the smeared field w.r.t. the thin
+                links, FP64 and FP32 (FP64 projection and its gradient), every
+                step checkpointed vs recomputed.
 Inputs are resident on the device before timing; times are CUDA events.
 """
 import json
@@ -250,6 +254,58 @@ def hyp32(args, torch, lq, fieldgen):
     return out
 
 
+# Gradient of the projection per link (FP64): Im tr(G'^dag P) 90, G_W 90,
+# Z = Herm(V^dag W) 210, invariants 8, two Hermitian inverses 180, p1 A + p3 12,
+# Herm(V^dag G_W) 210, C = H N / 2 216, A C + C A 396, Z C, C Z, (Z C) Z 612,
+# Y combination and Hermitian part 84, (G_W - 2 W Y) X 432, the two scaled
+# outputs 36; plus the projection itself again (APE_PROJECTION_FLOPS).
+APE_VJP_FLOPS = 90 + 90 + 210 + 8 + 180 + 12 + 210 + 216 + 396 + 612 + 84 + 432 + 36
+
+
+def apeforce24(args, torch, lq, fieldgen):
+    import bench
+    dims = (24, 24, 24, 48)
+    V = int(np.prod(dims))
+    n, alpha = 3, 0.6
+    out = {"metric": "APE force link-updates/s (3 steps, Wilson action)", "unit": "link-updates/s",
+           "config": {"workload": "24^3x48, exp(i*0.3*H) links seed 4, 3 APE steps alpha=0.6 in 4 dims, beta=6"}}
+    mhz = 2070.0
+    p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
+    p32 = 2.0 * bench.FP32_FMA_PER_CLK * mhz * 1e6
+    for name, prec in (("f64", lq.LQ_F64), ("f32", lq.LQ_F32)):
+        f, _ = _field(lq, fieldgen, dims, 4, prec)
+        F = lq.Field(f.geom, lq.LQ_LINKS, prec)
+        # per link and step: forward recompute (mix + projection), backward link
+        # kernel (mix + projection + its gradient), staple gather
+        proj64 = 2 * APE_PROJECTION_FLOPS + APE_VJP_FLOPS
+        algebra = n * (2 * APE_MIX_FLOPS + BWD_GATHER_FLOPS) + WILSON_GRAD_FLOPS + FORCE_FLOPS
+        flops64 = n * proj64 + (algebra if prec == lq.LQ_F64 else 0)
+        flops32 = 0 if prec == lq.LQ_F64 else algebra
+        res = {}
+        for every in (1, 3):
+            t = _events(torch, lambda: lq.ape_backward(f, alpha, n, (0, 1, 2, 3), F, beta=6.0,
+                                                       checkpoint_every=every), args.steps, args.warmup)
+            res[f"checkpoint_every_{every}"] = {"ms": t, "value": n * V * 4 / (t * 1e-3)}
+        t1 = res["checkpoint_every_1"]["ms"] * 1e-3
+        res["roofline"] = {"bound": "alu", "pipe": "fp64", "unit": "TFLOP/s",
+                           "fp64_flops_per_link": flops64, "fp32_flops_per_link": flops32,
+                           "achieved": flops64 * 4 * V / t1 / 1e12, "peak": p64 / 1e12,
+                           "frac": flops64 * 4 * V / t1 / p64,
+                           "t_bound_ms": {"fp64": 1e3 * flops64 * 4 * V / p64, "fp32": 1e3 * flops32 * 4 * V / p32},
+                           "peak_source": f"derived: {bench.FP64_FMA_PER_CLK} FP64 FMA/clk x 2 x {mhz:.0f} MHz",
+                           "note": "checkpoint_every=1; flops of the forward recompute included; Newton "
+                                   "refinements of square roots and reciprocals not counted"}
+        g = lq.Field(f.geom, lq.LQ_LINKS, prec)
+        g.tensor.copy_(f.tensor)
+        res["forward_ms"] = _events(torch, lambda: lq.ape_smear(g, alpha, n, (0, 1, 2, 3)), args.steps, args.warmup)
+        out[name] = res
+        del f, F, g
+        torch.cuda.empty_cache()
+    out["value"] = out["f64"]["checkpoint_every_1"]["value"]
+    out["dtype"] = "f64"
+    return out
+
+
 def micro16(args, torch, lq, fieldgen):
     dims = (16, 16, 16, 32)
     V = int(np.prod(dims))
@@ -290,7 +346,7 @@ def run(args):
     import paper_1105_2279_gb300 as lq
     torch.cuda.set_device(0)
     fn = {"batch64": batch64, "backward24": backward24, "micro16": micro16, "jacobi32": jacobi32,
-          "ape48": ape48, "hyp32": hyp32}[args.workload]
+          "ape48": ape48, "hyp32": hyp32, "apeforce24": apeforce24}[args.workload]
     res = fn(args, torch, lq, fieldgen)
     res.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                 "data": "synthetic", "workload_mode": args.workload})

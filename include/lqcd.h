@@ -317,6 +317,23 @@ lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, in
  * dirs_mask in [1, 15]; links outside dirs are unchanged. */
 lq_status lq_ape_smear(lq_field* links_inout, double alpha, int n_steps, unsigned dirs_mask, void* stream);
 
+/* Gradient of a scalar S(ape^n(U)) with respect to the thin links U: the
+ * fat-link force of APE smearing (the paper has no counterpart).  Arguments,
+ * outputs, checkpoints, scratch and errors as in lq_stout_backward, with
+ * alpha and dirs_mask as in lq_ape_smear (grad_seed NULL => the Wilson
+ * action of the smeared field at `beta`).  Per step and smeared link, the
+ * gradient G' at U' = P(V) goes to G_V through the projection:
+ *   U' = W z, z = (det W)^(-1/3):  G_W = conj(z) G' + (i/3) Im tr(G'^dag U') W
+ *   W = V (V^dag V)^(-1/2):       G_V = (G_W - 2 W Y) Z^-1,  Z = (V^dag V)^(1/2),
+ *                                 Y the solution of Z Y + Y Z = Herm(V^dag G_W)
+ * and from G_V to the links: (1 - alpha) G_V on U_mu(x) itself and
+ * alpha / (2 (d - 1)) G_V through each staple, as in the stout force.
+ * FP32 links: staples, mixing and staple gradients in FP32, the projection
+ * and its gradient in FP64.  V must be non-singular. */
+lq_status lq_ape_backward(const lq_field* thin_links, double alpha, int n_steps, unsigned dirs_mask,
+                          const lq_field* grad_seed, double beta, lq_field* force_out,
+                          lq_field* grad_out, const lq_backward_opts* opts, void* stream);
+
 /* HYP smearing (Hasenfratz and Knechtli, Phys. Rev. D 64 (2001) 034504; the
  * paper has no counterpart), n_steps steps in place on a LINKS field, all
  * four directions: three nested APE-type levels with weights a3 (innermost,

@@ -360,6 +360,18 @@ def stout_backward(thin, rho, n_steps, dirs, force_out, grad_seed=None, beta=6.0
                                       byref(o), _stream(stream)), "lq_stout_backward")
 
 
+def ape_backward(thin, alpha, n_steps, dirs, force_out, grad_seed=None, beta=6.0, grad_out=None,
+                 checkpoint_every=1, stream=None):
+    o = LqBackwardOpts()
+    o.struct_size = ctypes.sizeof(LqBackwardOpts)
+    o.checkpoint_every = int(checkpoint_every)
+    _check(L.load().lq_ape_backward(thin.handle, float(alpha), int(n_steps), dirs_mask(dirs),
+                                    grad_seed.handle if grad_seed is not None else None, float(beta),
+                                    force_out.handle if force_out is not None else None,
+                                    grad_out.handle if grad_out is not None else None,
+                                    byref(o), _stream(stream)), "lq_ape_backward")
+
+
 def tune(cache_path=None):
     _check(L.load().lq_tune(cache_path.encode() if cache_path else None), "lq_tune")
 
@@ -428,6 +440,31 @@ def _autograd():
             stout_backward(thin, rho, n_steps, dirs, None, grad_seed=seed, grad_out=gout)
             return gout.tensor, None, None, None, None
 
+    class ApeSmear(torch.autograd.Function):
+        """U -> ape^n(U) on a links tensor [4, 9, V, 2]; gradients as in StoutSmear."""
+
+        @staticmethod
+        def forward(ctx, links, dims, alpha, n_steps, dirs):
+            geom = Geometry(dims)
+            prec = _prec_of(links)
+            out = torch.empty_like(links)
+            out.copy_(links)
+            ape_smear(Field(geom, LQ_LINKS, prec, tensor=out), alpha, n_steps, dirs)
+            ctx.save_for_backward(links)
+            ctx.args = (dims, alpha, n_steps, dirs, prec)
+            return out
+
+        @staticmethod
+        def backward(ctx, grad):
+            (links,) = ctx.saved_tensors
+            dims, alpha, n_steps, dirs, prec = ctx.args
+            geom = Geometry(dims)
+            thin = Field(geom, LQ_LINKS, prec, tensor=links.contiguous())
+            seed = Field(geom, LQ_LINKS, prec, tensor=grad.contiguous())
+            gout = Field(geom, LQ_LINKS, prec)
+            ape_backward(thin, alpha, n_steps, dirs, None, grad_seed=seed, grad_out=gout)
+            return gout.tensor, None, None, None, None
+
     class WilsonAction(torch.autograd.Function):
         """S = beta sum_x sum_{mu<nu} (1 - Re tr P_{mu nu}(x)/3) of a links tensor (FP64 scalar)."""
 
@@ -451,11 +488,15 @@ def _autograd():
             stout_backward(thin, 0.0, 0, 15, None, beta=beta * float(grad), grad_out=gout)
             return gout.tensor, None, None
 
-    return StoutSmear, WilsonAction
+    return StoutSmear, WilsonAction, ApeSmear
 
 
 def stout_smear_autograd(links, dims, rho, n_steps, dirs=(0, 1, 2, 3)):
     return _autograd()[0].apply(links, tuple(dims), float(rho), int(n_steps), dirs_mask(dirs))
+
+
+def ape_smear_autograd(links, dims, alpha, n_steps, dirs=(0, 1, 2, 3)):
+    return _autograd()[2].apply(links, tuple(dims), float(alpha), int(n_steps), dirs_mask(dirs))
 
 
 def wilson_action_autograd(links, dims, beta):

@@ -47,6 +47,47 @@ __global__ void __launch_bounds__(256) k_ape(const typename vec2<R>::type* __res
 
 using namespace lq;
 
+namespace lq {
+
+lq_status ape_run_steps(void* links, void* work, const lq_geom& geom, int prec, size_t bytes, double alpha,
+                        int n_steps, unsigned dirs_mask, cudaStream_t s) {
+  if (n_steps == 0) return LQ_OK;
+  const GeomArgs g = geom_args(geom);
+  ApeDirs ad;
+  int nd = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    if ((dirs_mask >> mu) & 1u) ad.mu[nd++] = mu;
+  for (int j = nd; j < 4; ++j) ad.mu[j] = 0;
+  const double coef = nd > 1 ? alpha / (2.0 * (nd - 1)) : 0.0;   // one direction: no staples
+  const size_t db = bytes / 4;
+  lq_status st = LQ_OK;
+  for (int mu = 0; mu < 4 && st == LQ_OK; ++mu)   // unsmeared directions pass through both buffers
+    if (!((dirs_mask >> mu) & 1u))
+      st = cuda_check(cudaMemcpyAsync((char*)work + mu * db, (const char*)links + mu * db, db,
+                                      cudaMemcpyDeviceToDevice, s),
+                      "lq_ape_smear pass-through copy");
+  const dim3 grid((unsigned)(((g.V + 127) / 128) * nd));
+  for (int k = 0; k < n_steps && st == LQ_OK; ++k) {
+    const void* in = (k % 2 == 0) ? links : work;
+    void* out = (k % 2 == 0) ? work : links;
+    if (prec == LQ_F64)
+      k_ape<double><<<grid, 128, 0, s>>>((const double2*)in, (double2*)out, g, 1.0 - alpha, coef, dirs_mask, nd, ad);
+    else
+      k_ape<float><<<grid, 128, 0, s>>>((const float2*)in, (float2*)out, g, (float)(1.0 - alpha), (float)coef,
+                                        dirs_mask, nd, ad);
+    st = launch_check("lq_ape_smear kernel");
+  }
+  if (st == LQ_OK && n_steps % 2 == 1)
+    for (int mu = 0; mu < 4 && st == LQ_OK; ++mu)
+      if ((dirs_mask >> mu) & 1u)
+        st = cuda_check(cudaMemcpyAsync((char*)links + mu * db, (const char*)work + mu * db, db,
+                                        cudaMemcpyDeviceToDevice, s),
+                        "lq_ape_smear result copy");
+  return st;
+}
+
+}  // namespace lq
+
 extern "C" lq_status lq_ape_smear(lq_field* links, double alpha, int n_steps, unsigned dirs_mask, void* stream) {
   clear_error();
   lq_status st = check_links(links, "lq_ape_smear");
@@ -58,38 +99,9 @@ extern "C" lq_status lq_ape_smear(lq_field* links, double alpha, int n_steps, un
   }
   if (n_steps == 0) return LQ_OK;
   cudaStream_t s = as_stream(stream);
-  const GeomArgs g = geom_args(links->geom);
-  ApeDirs ad;
-  int nd = 0;
-  for (int mu = 0; mu < 4; ++mu)
-    if ((dirs_mask >> mu) & 1u) ad.mu[nd++] = mu;
-  for (int j = nd; j < 4; ++j) ad.mu[j] = 0;
-  const double coef = nd > 1 ? alpha / (2.0 * (nd - 1)) : 0.0;   // one direction: no staples
   void* work = nullptr;
   if ((st = scratch_alloc(&work, links->bytes, s, "lq_ape_smear workspace")) != LQ_OK) return st;
-  const size_t db = links->bytes / 4;
-  for (int mu = 0; mu < 4 && st == LQ_OK; ++mu)   // unsmeared directions pass through both buffers
-    if (!((dirs_mask >> mu) & 1u))
-      st = cuda_check(cudaMemcpyAsync((char*)work + mu * db, (const char*)links->ptr + mu * db, db,
-                                      cudaMemcpyDeviceToDevice, s),
-                      "lq_ape_smear pass-through copy");
-  const dim3 grid((unsigned)(((g.V + 127) / 128) * nd));
-  for (int k = 0; k < n_steps && st == LQ_OK; ++k) {
-    const void* in = (k % 2 == 0) ? links->ptr : work;
-    void* out = (k % 2 == 0) ? work : links->ptr;
-    if (links->prec == LQ_F64)
-      k_ape<double><<<grid, 128, 0, s>>>((const double2*)in, (double2*)out, g, 1.0 - alpha, coef, dirs_mask, nd, ad);
-    else
-      k_ape<float><<<grid, 128, 0, s>>>((const float2*)in, (float2*)out, g, (float)(1.0 - alpha), (float)coef,
-                                        dirs_mask, nd, ad);
-    st = launch_check("lq_ape_smear kernel");
-  }
-  if (st == LQ_OK && n_steps % 2 == 1)
-    for (int mu = 0; mu < 4 && st == LQ_OK; ++mu)
-      if ((dirs_mask >> mu) & 1u)
-        st = cuda_check(cudaMemcpyAsync((char*)links->ptr + mu * db, (const char*)work + mu * db, db,
-                                        cudaMemcpyDeviceToDevice, s),
-                        "lq_ape_smear result copy");
+  st = ape_run_steps(links->ptr, work, links->geom, links->prec, links->bytes, alpha, n_steps, dirs_mask, s);
   scratch_free(work, s);
   return st;
 }

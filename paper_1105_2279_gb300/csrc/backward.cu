@@ -12,30 +12,21 @@
 //                 (the gradient w.r.t. the bare staple sum S).
 //   k_bwd_staple: per link, adds the six staple-insertion terms of K of the
 //                 neighbouring links (the six-term sum of the stout force).
+// The APE force (lq_ape_backward) runs the same recursion with its own link
+// kernel: per smeared link V = (1 - alpha) U + c S, U' = P(V), so
+//   k_ape_bwd_link: G_V from G' through the projection (su3_project.cuh),
+//                   writes G_U(local) = (1 - alpha) G_V and K = c G_V,
+// followed by the same k_bwd_staple.
 #include <algorithm>
 #include <vector>
 
 #include "lq_internal.h"
 #include "stout_core.cuh"
+#include "su3_project.cuh"
 
 namespace lq {
 
 template <typename R> using V2 = typename vec2<R>::type;
-
-template <typename R>
-__device__ __forceinline__ M3<R> qh_full(const QH<R>& q) {
-  M3<R> m;
-  m.e[0] = mkc<R>(q.d0, 0);
-  m.e[4] = mkc<R>(q.d1, 0);
-  m.e[8] = mkc<R>(q.d2, 0);
-  m.e[1] = q.o01;
-  m.e[2] = q.o02;
-  m.e[5] = q.o12;
-  m.e[3] = cconj(q.o01);
-  m.e[6] = cconj(q.o02);
-  m.e[7] = cconj(q.o12);
-  return m;
-}
 
 // sum_ij conj(A_ij) B_ij = tr(A^dag B)
 template <typename R> __device__ __forceinline__ cx<R> tr_dn(const M3<R>& a, const M3<R>& b) {
@@ -100,6 +91,46 @@ __global__ void __launch_bounds__(128) k_bwd_link(const V2<R>* __restrict__ U, c
   mac_dn(Gl, GO, C);
   st_m3<R>(Gout + off, V, Gl);
   st_m3<R>(K + off, V, m_rscale(mul_nn(GO, Umu), rho));
+}
+
+// APE step, per smeared link: V recomputed exactly as in the forward kernel
+// (staples and mixing in the field precision), the projection's gradient in FP64.
+template <typename R>
+__global__ void __launch_bounds__(128) k_ape_bwd_link(const V2<R>* __restrict__ U, const V2<R>* __restrict__ Gp,
+                                                      V2<R>* __restrict__ Gout, V2<R>* __restrict__ K, GeomArgs g,
+                                                      R keep, R coef, unsigned dirs) {
+  const long long V = g.V;
+  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const int s = (int)sl;
+  const int mu = blockIdx.y;
+  const long long off = (long long)mu * 9 * V + s;
+  if (!((dirs >> mu) & 1u)) {  // not smeared: the gradient passes through
+    st_m3<R>(Gout + off, V, ld_m3<R>(Gp + off, V));
+    return;
+  }
+  int c[4];
+  site_coords(g, s, c);
+  const M3<R> C = staple_sum<R>(U, g, s, c, mu, dirs);
+  const M3<R> Umu = ld_m3<R>(U + off, V);
+  const M3<R> Gpm = ld_m3<R>(Gp + off, V);
+  M3<double> v, gp;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const cx<R> e = mkc<R>(fmaR(coef, C.e[i].re, keep * Umu.e[i].re), fmaR(coef, C.e[i].im, keep * Umu.e[i].im));
+    v.e[i] = mkc(to_f64(e.re), to_f64(e.im));
+    gp.e[i] = mkc(to_f64(Gpm.e[i].re), to_f64(Gpm.e[i].im));
+  }
+  const M3<double> gv = project_su3_vjp_f64<sizeof(R) == 4 ? 1 : 2>(v, gp);
+  M3<R> gl, kk;
+  const double kd = (double)keep, cd = (double)coef;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    gl.e[i] = mkc<R>(from_f64<R>(kd * gv.e[i].re), from_f64<R>(kd * gv.e[i].im));
+    kk.e[i] = mkc<R>(from_f64<R>(cd * gv.e[i].re), from_f64<R>(cd * gv.e[i].im));
+  }
+  st_m3<R>(Gout + off, V, gl);
+  st_m3<R>(K + off, V, kk);
 }
 
 template <typename R>
@@ -183,9 +214,13 @@ struct Bufs {
   }
 };
 
+enum class Smearing { kStout, kApe };
+
+// w: rho (stout) or alpha (APE)
 template <typename R>
-static lq_status backward_impl(const lq_field* thin, double rho, int n, unsigned dirs, const lq_field* seed, double beta,
-                               lq_field* force, lq_field* grad_out, int every, cudaStream_t s) {
+static lq_status backward_impl(Smearing kind, const lq_field* thin, double w, int n, unsigned dirs,
+                               const lq_field* seed, double beta, lq_field* force, lq_field* grad_out, int every,
+                               cudaStream_t s) {
   const GeomArgs g = geom_args(thin->geom);
   const long long V = g.V;
   const size_t fb = thin->bytes;
@@ -207,6 +242,13 @@ static lq_status backward_impl(const lq_field* thin, double rho, int n, unsigned
   TuneChoice tc = stout_default_choice(thin->prec);
   // recomputed fields follow lq_stout_smear's default (FP32 links are re-projected)
   const int reproject = thin->prec == LQ_F32 ? 1 : 0;
+  auto run_steps = [&](void* links, int steps) -> lq_status {
+    if (kind == Smearing::kApe) return ape_run_steps(links, w1, thin->geom, thin->prec, fb, w, steps, dirs, s);
+    return stout_run_steps(links, w1, thin->geom, thin->prec, w, steps, dirs, reproject, tc, s);
+  };
+  int nd = 0;
+  for (int mu = 0; mu < 4; ++mu) nd += (dirs >> mu) & 1u;
+  const double ape_coef = nd > 1 ? w / (2.0 * (nd - 1)) : 0.0;   // as in lq_ape_smear
   // forward: U^(j) from the nearest stored checkpoint at or below j (stored
   // indices are multiples of `every` below n), into dst
   auto forward_to = [&](int j, void* dst) -> lq_status {
@@ -214,13 +256,13 @@ static lq_status backward_impl(const lq_field* thin, double rho, int n, unsigned
     if (j0 >= n) j0 = ((n - 1) / every) * every;
     lq_status st2 = cuda_check(cudaMemcpyAsync(dst, ck[j0], fb, cudaMemcpyDeviceToDevice, s), "lq_stout_backward copy");
     if (st2 != LQ_OK) return st2;
-    return stout_run_steps(dst, w1, thin->geom, thin->prec, rho, j - j0, dirs, reproject, tc, s);
+    return run_steps(dst, j - j0);
   };
   for (int j = every; j < n; j += every) {  // ck[j] = `every` steps from ck[j - every]
     if ((st = cuda_check(cudaMemcpyAsync(ck[j], ck[j - every], fb, cudaMemcpyDeviceToDevice, s),
                          "lq_stout_backward checkpoint")))
       return st;
-    if ((st = stout_run_steps(ck[j], w1, thin->geom, thin->prec, rho, every, dirs, reproject, tc, s))) return st;
+    if ((st = run_steps(ck[j], every))) return st;
   }
   // seed at U^(n)
   if (seed) {
@@ -243,8 +285,12 @@ static lq_status backward_impl(const lq_field* thin, double rho, int n, unsigned
       Uj = w0;
     }
     dim3 grid((unsigned)((V + 127) / 128), 4);
-    k_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g, (R)rho, dirs);
-    if ((st = launch_check("k_bwd_link"))) return st;
+    if (kind == Smearing::kApe)
+      k_ape_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g,
+                                             (R)(1.0 - w), (R)ape_coef, dirs);
+    else
+      k_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g, (R)w, dirs);
+    if ((st = launch_check("backward link kernel"))) return st;
     k_bwd_staple<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Kb, (V2<R>*)Gb, g, dirs);
     if ((st = launch_check("k_bwd_staple"))) return st;
     std::swap(Ga, Gb);
@@ -264,38 +310,75 @@ static lq_status backward_impl(const lq_field* thin, double rho, int n, unsigned
 
 using namespace lq;
 
-extern "C" lq_status lq_stout_backward(const lq_field* thin, double rho, int n_steps, unsigned dirs_mask,
-                                       const lq_field* grad_seed, double beta, lq_field* force_out, lq_field* grad_out,
-                                       const lq_backward_opts* opts, void* stream) {
-  clear_error();
-  lq_status st = check_links(thin, "lq_stout_backward");
+// Argument checks shared by the two force entry points.
+static lq_status check_backward(const char* who, const lq_field* thin, unsigned dirs_mask, int n_steps, double beta,
+                                const lq_field* grad_seed, const lq_field* force_out, const lq_field* grad_out) {
+  lq_status st = check_links(thin, who);
   if (st != LQ_OK) return st;
-  if ((st = check_dirs(dirs_mask, "lq_stout_backward")) != LQ_OK) return st;
-  if (!(rho >= 0.0) || rho > 1e6 || n_steps < 0 || !(beta == beta)) {
-    set_error("lq_stout_backward: rho must be finite >= 0, n_steps >= 0, beta finite");
+  if ((st = check_dirs(dirs_mask, who)) != LQ_OK) return st;
+  if (n_steps < 0 || !(beta == beta)) {
+    set_error("%s: n_steps must be >= 0 and beta finite", who);
     return LQ_ERR_ARG;
   }
   if (!force_out && !grad_out) {
-    set_error("lq_stout_backward: neither force_out nor grad_out given");
+    set_error("%s: neither force_out nor grad_out given", who);
     return LQ_ERR_ARG;
   }
   const lq_field* outs[3] = {grad_seed, force_out, grad_out};
   for (const lq_field* f : outs) {
     if (!f) continue;
     if (f->kind != LQ_LINKS || f->prec != thin->prec || !same_geom(f->geom, thin->geom)) {
-      set_error("lq_stout_backward: seed/force/grad fields must be LINKS of the thin field's geometry and precision");
+      set_error("%s: seed/force/grad fields must be LINKS of the thin field's geometry and precision", who);
       return LQ_ERR_GEOM;
     }
     if (f->ptr == thin->ptr) {
-      set_error("lq_stout_backward: outputs must not alias the thin links");
+      set_error("%s: outputs must not alias the thin links", who);
       return LQ_ERR_ARG;
     }
   }
-  int every = 1;
+  return LQ_OK;
+}
+
+static int checkpoint_every(const lq_backward_opts* opts) {
   if (opts && opts->struct_size >= (int)sizeof(lq_backward_opts) && opts->checkpoint_every > 0)
-    every = opts->checkpoint_every;
+    return opts->checkpoint_every;
+  return 1;
+}
+
+extern "C" lq_status lq_stout_backward(const lq_field* thin, double rho, int n_steps, unsigned dirs_mask,
+                                       const lq_field* grad_seed, double beta, lq_field* force_out, lq_field* grad_out,
+                                       const lq_backward_opts* opts, void* stream) {
+  clear_error();
+  lq_status st = check_backward("lq_stout_backward", thin, dirs_mask, n_steps, beta, grad_seed, force_out, grad_out);
+  if (st != LQ_OK) return st;
+  if (!(rho >= 0.0) || rho > 1e6) {
+    set_error("lq_stout_backward: rho must be finite >= 0");
+    return LQ_ERR_ARG;
+  }
+  const int every = checkpoint_every(opts);
   cudaStream_t s = as_stream(stream);
   if (thin->prec == LQ_F64)
-    return backward_impl<double>(thin, rho, n_steps, dirs_mask, grad_seed, beta, force_out, grad_out, every, s);
-  return backward_impl<float>(thin, rho, n_steps, dirs_mask, grad_seed, beta, force_out, grad_out, every, s);
+    return backward_impl<double>(Smearing::kStout, thin, rho, n_steps, dirs_mask, grad_seed, beta, force_out,
+                                 grad_out, every, s);
+  return backward_impl<float>(Smearing::kStout, thin, rho, n_steps, dirs_mask, grad_seed, beta, force_out, grad_out,
+                              every, s);
+}
+
+extern "C" lq_status lq_ape_backward(const lq_field* thin, double alpha, int n_steps, unsigned dirs_mask,
+                                     const lq_field* grad_seed, double beta, lq_field* force_out, lq_field* grad_out,
+                                     const lq_backward_opts* opts, void* stream) {
+  clear_error();
+  lq_status st = check_backward("lq_ape_backward", thin, dirs_mask, n_steps, beta, grad_seed, force_out, grad_out);
+  if (st != LQ_OK) return st;
+  if (!(alpha == alpha) || alpha > 1e6 || alpha < -1e6) {
+    set_error("lq_ape_backward: alpha must be finite");
+    return LQ_ERR_ARG;
+  }
+  const int every = checkpoint_every(opts);
+  cudaStream_t s = as_stream(stream);
+  if (thin->prec == LQ_F64)
+    return backward_impl<double>(Smearing::kApe, thin, alpha, n_steps, dirs_mask, grad_seed, beta, force_out,
+                                 grad_out, every, s);
+  return backward_impl<float>(Smearing::kApe, thin, alpha, n_steps, dirs_mask, grad_seed, beta, force_out, grad_out,
+                              every, s);
 }

@@ -100,6 +100,10 @@ lq_status stout_run_steps(void* links, void* work, const lq_geom& g, int prec, d
                           int n_steps, unsigned dirs, int reproject, const TuneChoice& tc,
                           cudaStream_t s, void* wbuf = nullptr);
 TuneChoice stout_default_choice(int prec);
+// n APE steps in place on the link field `links` (bytes long), with `work` a
+// scratch field of the same size; the arithmetic of lq_ape_smear.
+lq_status ape_run_steps(void* links, void* work, const lq_geom& g, int prec, size_t bytes, double alpha,
+                        int n_steps, unsigned dirs, cudaStream_t s);
 // One stout step over the sites [s_begin, s_end) only (global-load kernel).
 lq_status stout_step_range(const void* in, void* out, const lq_geom& g, int prec, double rho, unsigned dirs,
                            int reproject, const TuneChoice& tc, long long s_begin, long long s_end,

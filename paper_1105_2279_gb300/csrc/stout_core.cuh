@@ -56,6 +56,22 @@ template <typename R> struct QH {
   cx<R> o01, o02, o12;
 };
 
+// the full matrix of a compact Hermitian one
+template <typename R>
+__device__ __forceinline__ M3<R> qh_full(const QH<R>& q) {
+  M3<R> m;
+  m.e[0] = mkc<R>(q.d0, 0);
+  m.e[4] = mkc<R>(q.d1, 0);
+  m.e[8] = mkc<R>(q.d2, 0);
+  m.e[1] = q.o01;
+  m.e[2] = q.o02;
+  m.e[5] = q.o12;
+  m.e[3] = cconj(q.o01);
+  m.e[6] = cconj(q.o02);
+  m.e[7] = cconj(q.o12);
+  return m;
+}
+
 // Q = (i/2)(Omega^dag - Omega) - (i/6) tr(Omega^dag - Omega)
 template <typename R> __device__ __forceinline__ QH<R> q_from_omega(const M3<R>& om) {
   QH<R> q;

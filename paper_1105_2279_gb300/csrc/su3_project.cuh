@@ -64,10 +64,19 @@ static __device__ __noinline__ M3<double> polar_newton(M3<double> y) {
   return y;
 }
 
+// The pieces of P(V) = W z: the polar factor W, the phase z = exp(-i arg(det V) / 3),
+// A = V^dag V (compact Hermitian) and |det V| (= det (V^dag V)^(1/2)).
+struct PolarParts {
+  M3<double> W;
+  cx<double> z;
+  QH<double> A;
+  double absdet;
+};
+
 // NR: Newton steps after the FP32 seeds of the square roots, reciprocals and
 // the cube root (1 on FP32 links, ~1e-13 relative; 2 on FP64 links).
 template <int NR>
-__device__ __forceinline__ M3<double> project_su3_f64(const M3<double>& v) {
+__device__ __forceinline__ PolarParts polar_parts_f64(const M3<double>& v) {
   // A = V^dag V: A_ij = sum_k conj(V_ki) V_kj
   double a00 = 0, a11 = 0, a22 = 0;
   cx<double> a01 = mkc(0.0, 0.0), a02 = a01, a12 = a01;
@@ -170,10 +179,118 @@ __device__ __forceinline__ M3<double> project_su3_f64(const M3<double>& v) {
     w = mkc((2.0 * w.re + t2.re) * (1.0 / 3.0), (2.0 * w.im + t2.im) * (1.0 / 3.0));
   }
   const double wn = rsqrt_nr<NR>(cnorm2(w));
-  const cx<double> ph = mkc(w.re * wn, -w.im * wn);
+  PolarParts pp;
+  pp.W = W;
+  pp.z = mkc(w.re * wn, -w.im * wn);
+  pp.A = A;
+  pp.absdet = cnorm2(det) * ar;
+  return pp;
+}
+
+template <int NR>
+__device__ __forceinline__ M3<double> project_su3_f64(const M3<double>& v) {
+  const PolarParts pp = polar_parts_f64<NR>(v);
+  M3<double> P;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) W.e[i] = cmul(W.e[i], ph);
-  return W;
+  for (int i = 0; i < 9; ++i) P.e[i] = cmul(pp.W.e[i], pp.z);
+  return P;
+}
+
+// Inverse of a Hermitian matrix from its adjugate (inverse_ij = cofactor_ji / det).
+__device__ __forceinline__ QH<double> qh_inverse(const QH<double>& h) {
+  const double a = h.d0, d = h.d1, f = h.d2;
+  const cx<double> b = h.o01, c = h.o02, e = h.o12;
+  QH<double> r;
+  r.d0 = d * f - cnorm2(e);
+  r.d1 = a * f - cnorm2(c);
+  r.d2 = a * d - cnorm2(b);
+  r.o01 = csub(cmul(c, cconj(e)), cscale(b, f));
+  r.o02 = csub(cmul(b, e), cscale(c, d));
+  r.o12 = csub(cmul(c, cconj(b)), cscale(e, a));
+  // det = a (d f - |e|^2) - f |b|^2 - d |c|^2 + 2 Re(b e conj(c))
+  const cx<double> be = cmul(b, e);
+  const double det = a * r.d0 - f * cnorm2(b) - d * cnorm2(c) + 2.0 * (be.re * c.re + be.im * c.im);
+  const double id = 1.0 / det;
+  r.d0 *= id;
+  r.d1 *= id;
+  r.d2 *= id;
+  r.o01 = cscale(r.o01, id);
+  r.o02 = cscale(r.o02, id);
+  r.o12 = cscale(r.o12, id);
+  return r;
+}
+
+// Hermitian part (M + M^dag)/2 in compact form
+__device__ __forceinline__ QH<double> herm_part(const M3<double>& m) {
+  QH<double> h;
+  h.d0 = m.e[0].re;
+  h.d1 = m.e[4].re;
+  h.d2 = m.e[8].re;
+  h.o01 = mkc(0.5 * (m.e[1].re + m.e[3].re), 0.5 * (m.e[1].im - m.e[3].im));
+  h.o02 = mkc(0.5 * (m.e[2].re + m.e[6].re), 0.5 * (m.e[2].im - m.e[6].im));
+  h.o12 = mkc(0.5 * (m.e[5].re + m.e[7].re), 0.5 * (m.e[5].im - m.e[7].im));
+  return h;
+}
+
+// Gradient through P: given G_P (G = dS/dRe + i dS/dIm, dS = Re tr(G^dag dP)),
+// returns G_V.  With Z = (V^dag V)^(1/2) (so W = V Z^-1) and p1, p2, p3 the
+// elementary symmetric functions of Z's eigenvalues s_k:
+//   P = W z, z = (det W)^(-1/3), dz = -(z/3) tr(W^dag dW) on the unitary W:
+//       G_W = conj(z) G_P + (i/3) Im tr(G_P^dag P) W
+//   W = V X, X = Z^-1:  G_V = G_W X + 2 V dX[H],  H = Herm(V^dag G_W),
+//       dX[H] the derivative of X = A^(-1/2) along dA = H; dX = -X Y X
+//       with Y the solution of the Lyapunov equation Z Y + Y Z = H.
+//   The Lyapunov equation in closed form (no eigenvectors): with L, R the
+//   left and right multiplications by Z, 1/(x + y) reduces modulo the
+//   characteristic polynomial t^3 - p1 t^2 + p2 t - p3 of both to
+//     (x^2 - x y + y^2 - p1 x + p1 y + p2) / (2 (p1 y^2 + p3)),
+//   so Y = A C + C A - Z C Z - p1 (Z C - C Z) + p2 C with C = H (p1 A + p3)^-1 / 2
+//   (A = Z^2).  Its terms carry magnitudes up to s_max^2 |C|, so it loses
+//   about s_max / s_min in relative accuracy.
+// Then G_V = (G_W - 2 W Y) X.  All FP64.
+template <int NR>
+__device__ __forceinline__ M3<double> project_su3_vjp_f64(const M3<double>& v, const M3<double>& gp) {
+  const PolarParts pp = polar_parts_f64<NR>(v);
+  double kim = 0.0;   // Im tr(G_P^dag P) = Im sum conj(G_P) P
+  M3<double> gw;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const cx<double> p = cmul(pp.W.e[i], pp.z);
+    kim = fma(gp.e[i].re, p.im, fma(-gp.e[i].im, p.re, kim));
+  }
+  const double k3 = kim * (1.0 / 3.0);
+  const cx<double> zc = cconj(pp.z);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const cx<double> a = cmul(zc, gp.e[i]);
+    gw.e[i] = mkc(a.re - k3 * pp.W.e[i].im, a.im + k3 * pp.W.e[i].re);
+  }
+  const QH<double> Zh = herm_part(mul_dn(v, pp.W));
+  const double p1 = Zh.d0 + Zh.d1 + Zh.d2;
+  const double p2 = 0.5 * (p1 * p1 - (pp.A.d0 + pp.A.d1 + pp.A.d2));
+  const double p3 = pp.absdet;
+  const M3<double> X = qh_full(qh_inverse(Zh));
+  const M3<double> Z = qh_full(Zh), A = qh_full(pp.A);
+  QH<double> Bh = pp.A;   // p1 A + p3
+  Bh.d0 = fma(p1, Bh.d0, p3);
+  Bh.d1 = fma(p1, Bh.d1, p3);
+  Bh.d2 = fma(p1, Bh.d2, p3);
+  Bh.o01 = cscale(Bh.o01, p1);
+  Bh.o02 = cscale(Bh.o02, p1);
+  Bh.o12 = cscale(Bh.o12, p1);
+  const M3<double> N = qh_full(qh_inverse(Bh));
+  const M3<double> C = m_rscale(mul_nn(qh_full(herm_part(mul_dn(v, gw))), N), 0.5);
+  const M3<double> ZC = mul_nn(Z, C), CZ = mul_nn(C, Z);
+  M3<double> Y = mul_nn(A, C);
+  mac_nn(Y, C, A);
+  Y = m_sub(Y, mul_nn(ZC, Z));
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const cx<double> d = csub(ZC.e[i], CZ.e[i]);
+    Y.e[i] = mkc(fma(p2, C.e[i].re, fma(-p1, d.re, Y.e[i].re)), fma(p2, C.e[i].im, fma(-p1, d.im, Y.e[i].im)));
+  }
+  const M3<double> Yh = qh_full(herm_part(Y));
+  return mul_nn(m_sub(gw, m_rscale(mul_nn(pp.W, Yh), 2.0)), X);
 }
 
 }  // namespace lq
