@@ -37,6 +37,9 @@ operations (``np.roll`` for shifts, ``@`` for 3x3 products):
 * ``hyp``      -- HYP smearing (Hasenfratz and Knechtli, Phys. Rev. D 64
   (2001) 034504): three nested APE-type levels with staples confined to the
   hypercubes attached to the link.
+* ``hyp_force`` -- reverse-mode gradient through HYP steps: the three levels
+  backwards, each through the projection's gradient of ``ape_force`` and a
+  two-field staple gradient.
 
 Field convention: a link field is an array of shape (Lt, Lz, Ly, Lx, 4, 3, 3)
 complex128, i.e. site-major with x fastest, direction mu = 0,1,2,3 = x,y,z,t,
