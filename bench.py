@@ -237,7 +237,7 @@ def main():
     ap.add_argument("--variant", type=int, default=0,
                     help="step kernel: 0 auto-tuned (default), 1 global loads, 2 shared-memory staged (FP32)")
     ap.add_argument("--workload", default="stout48",
-                    choices=["stout48", "batch64", "backward24", "micro16", "jacobi32", "ape48", "hyp32", "apeforce24"],
+                    choices=["stout48", "batch64", "backward24", "micro16", "jacobi32", "ape48", "hyp32", "apeforce24", "hypforce24"],
                     help="stout48 (default, the headline line); the others print their own JSON line")
     args = ap.parse_args()
     if args.workload != "stout48" and args.impl == "ours":

@@ -24,6 +24,9 @@
                 Wilson action (beta = 6) of the smeared field w.r.t. the thin
                 links, FP64 and FP32 (FP64 projection and its gradient), every
                 step checkpointed vs recomputed.
+* hypforce24 -- 24^3 x 48, 2 HYP steps (0.75, 0.6, 0.3), gradient of the
+                Wilson action (beta = 6) of the smeared field w.r.t. the thin
+                links, FP64 and FP32 (FP64 projections and their gradients).
 Inputs are resident on the device before timing; times are CUDA events.
 """
 import json
@@ -306,6 +309,47 @@ def apeforce24(args, torch, lq, fieldgen):
     return out
 
 
+# HYP force per site and step.  Field precision: the forward step of the
+# checkpoint pass (HYP_MIX_FLOPS_PER_SITE), levels 3 and 2 recomputed in the
+# gradient step (12 x (4 x 198 + 36) + 12 x (8 x 198 + 36)), the sums of
+# levels 1, 2, 3 again in their gradient kernels (4 x (12 x 198 + 36) +
+# 12 x (8 x 198 + 36) + 12 x (4 x 198 + 36)), the gathers (12 x 12 + 12 x 24 +
+# 4 x 36 products).  FP64: 28 + 24 + 28 projections and 28 projection gradients.
+HYPF_MIX_FLOPS_PER_SITE = (HYP_MIX_FLOPS_PER_SITE + 12 * (4 * 198 + 36) + 12 * (8 * 198 + 36)
+                           + 4 * (12 * 198 + 36) + 12 * (8 * 198 + 36) + 12 * (4 * 198 + 36)
+                           + (12 * 12 + 12 * 24 + 4 * 36) * 198)
+HYPF_F64_FLOPS_PER_SITE = 80 * APE_PROJECTION_FLOPS + 28 * APE_VJP_FLOPS
+
+
+def hypforce24(args, torch, lq, fieldgen):
+    import bench
+    dims, n, w = (24, 24, 24, 48), 2, (0.75, 0.6, 0.3)
+    V = int(np.prod(dims))
+    out = {"metric": "HYP force link-updates/s (2 steps, Wilson action)", "unit": "link-updates/s",
+           "config": {"workload": "24^3x48, exp(i*0.3*H) links seed 4, 2 HYP steps (0.75, 0.6, 0.3), beta=6"}}
+    mhz = 2070.0
+    p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
+    for name, prec in (("f64", lq.LQ_F64), ("f32", lq.LQ_F32)):
+        f, _ = _field(lq, fieldgen, dims, 4, prec)
+        F = lq.Field(f.geom, lq.LQ_LINKS, prec)
+        t = _events(torch, lambda: lq.hyp_backward(f, *w, n, F, beta=6.0), args.steps, args.warmup)
+        f64_site = n * (HYPF_F64_FLOPS_PER_SITE + (HYPF_MIX_FLOPS_PER_SITE if prec == lq.LQ_F64 else 0))
+        ach = f64_site * V / (t * 1e-3)
+        g = lq.Field(f.geom, lq.LQ_LINKS, prec)
+        g.tensor.copy_(f.tensor)
+        tf = _events(torch, lambda: lq.hyp_smear(g, *w, n), args.steps, args.warmup)
+        out[name] = {"ms": t, "value": n * V * 4 / (t * 1e-3), "forward_ms": tf,
+                     "roofline": {"bound": "alu", "pipe": "fp64", "fp64_flops_per_link": f64_site / (4 * n),
+                                  "achieved": ach / 1e12, "peak": p64 / 1e12, "frac": ach / p64, "unit": "TFLOP/s",
+                                  "note": "every step checkpointed; Newton refinements of square roots and "
+                                          "reciprocals not counted"}}
+        del f, F, g
+        torch.cuda.empty_cache()
+    out["value"] = out["f64"]["value"]
+    out["dtype"] = "f64"
+    return out
+
+
 def micro16(args, torch, lq, fieldgen):
     dims = (16, 16, 16, 32)
     V = int(np.prod(dims))
@@ -346,7 +390,8 @@ def run(args):
     import paper_1105_2279_gb300 as lq
     torch.cuda.set_device(0)
     fn = {"batch64": batch64, "backward24": backward24, "micro16": micro16, "jacobi32": jacobi32,
-          "ape48": ape48, "hyp32": hyp32, "apeforce24": apeforce24}[args.workload]
+          "ape48": ape48, "hyp32": hyp32, "apeforce24": apeforce24,
+          "hypforce24": hypforce24}[args.workload]
     res = fn(args, torch, lq, fieldgen)
     res.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                 "data": "synthetic", "workload_mode": args.workload})

@@ -344,6 +344,22 @@ lq_status lq_ape_backward(const lq_field* thin_links, double alpha, int n_steps,
  * 24 colour-matrix fields of decorated links and one link field. */
 lq_status lq_hyp_smear(lq_field* links_inout, double a1, double a2, double a3, int n_steps, void* stream);
 
+/* Gradient of a scalar S(hyp^n(U)) with respect to the thin links U: the
+ * fat-link force of HYP smearing (the paper has no counterpart).  Arguments,
+ * outputs, checkpoints and errors as in lq_stout_backward, with the weights
+ * of lq_hyp_smear (all four directions smeared).  Per step the three levels
+ * run backwards: the gradient at each level's sum V goes through the
+ * projection's gradient of lq_ape_backward, then into the decorated links
+ * (or thin links) that the level's staples read, through the staple
+ * gradient with K = (level weight / staple count) G_V; each link also
+ * collects (1 - a_i) G_V of the sums it enters directly.  Staples, mixing
+ * and staple gradients in the field precision, projections and their
+ * gradients in FP64.  Scratch: 64 colour-matrix fields (decorated links and
+ * their gradients) besides the checkpoints. */
+lq_status lq_hyp_backward(const lq_field* thin_links, double a1, double a2, double a3, int n_steps,
+                          const lq_field* grad_seed, double beta, lq_field* force_out,
+                          lq_field* grad_out, const lq_backward_opts* opts, void* stream);
+
 /* ---- Jacobi smearing ([W] Sec. 6, Listing 1 and the operator K) ----------- */
 
 /* n_iter Jacobi smearing iterations of a quark field, in place:

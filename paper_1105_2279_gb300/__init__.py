@@ -372,6 +372,18 @@ def ape_backward(thin, alpha, n_steps, dirs, force_out, grad_seed=None, beta=6.0
                                     byref(o), _stream(stream)), "lq_ape_backward")
 
 
+def hyp_backward(thin, a1, a2, a3, n_steps, force_out, grad_seed=None, beta=6.0, grad_out=None,
+                 checkpoint_every=1, stream=None):
+    o = LqBackwardOpts()
+    o.struct_size = ctypes.sizeof(LqBackwardOpts)
+    o.checkpoint_every = int(checkpoint_every)
+    _check(L.load().lq_hyp_backward(thin.handle, float(a1), float(a2), float(a3), int(n_steps),
+                                    grad_seed.handle if grad_seed is not None else None, float(beta),
+                                    force_out.handle if force_out is not None else None,
+                                    grad_out.handle if grad_out is not None else None,
+                                    byref(o), _stream(stream)), "lq_hyp_backward")
+
+
 def tune(cache_path=None):
     _check(L.load().lq_tune(cache_path.encode() if cache_path else None), "lq_tune")
 
@@ -465,6 +477,31 @@ def _autograd():
             ape_backward(thin, alpha, n_steps, dirs, None, grad_seed=seed, grad_out=gout)
             return gout.tensor, None, None, None, None
 
+    class HypSmear(torch.autograd.Function):
+        """U -> hyp^n(U) on a links tensor [4, 9, V, 2]; gradients as in StoutSmear."""
+
+        @staticmethod
+        def forward(ctx, links, dims, weights, n_steps):
+            geom = Geometry(dims)
+            prec = _prec_of(links)
+            out = torch.empty_like(links)
+            out.copy_(links)
+            hyp_smear(Field(geom, LQ_LINKS, prec, tensor=out), *weights, n_steps)
+            ctx.save_for_backward(links)
+            ctx.args = (dims, weights, n_steps, prec)
+            return out
+
+        @staticmethod
+        def backward(ctx, grad):
+            (links,) = ctx.saved_tensors
+            dims, weights, n_steps, prec = ctx.args
+            geom = Geometry(dims)
+            thin = Field(geom, LQ_LINKS, prec, tensor=links.contiguous())
+            seed = Field(geom, LQ_LINKS, prec, tensor=grad.contiguous())
+            gout = Field(geom, LQ_LINKS, prec)
+            hyp_backward(thin, *weights, n_steps, None, grad_seed=seed, grad_out=gout)
+            return gout.tensor, None, None, None
+
     class WilsonAction(torch.autograd.Function):
         """S = beta sum_x sum_{mu<nu} (1 - Re tr P_{mu nu}(x)/3) of a links tensor (FP64 scalar)."""
 
@@ -488,7 +525,7 @@ def _autograd():
             stout_backward(thin, 0.0, 0, 15, None, beta=beta * float(grad), grad_out=gout)
             return gout.tensor, None, None
 
-    return StoutSmear, WilsonAction, ApeSmear
+    return StoutSmear, WilsonAction, ApeSmear, HypSmear
 
 
 def stout_smear_autograd(links, dims, rho, n_steps, dirs=(0, 1, 2, 3)):
@@ -497,6 +534,10 @@ def stout_smear_autograd(links, dims, rho, n_steps, dirs=(0, 1, 2, 3)):
 
 def ape_smear_autograd(links, dims, alpha, n_steps, dirs=(0, 1, 2, 3)):
     return _autograd()[2].apply(links, tuple(dims), float(alpha), int(n_steps), dirs_mask(dirs))
+
+
+def hyp_smear_autograd(links, dims, a1=0.75, a2=0.6, a3=0.3, n_steps=1):
+    return _autograd()[3].apply(links, tuple(dims), (float(a1), float(a2), float(a3)), int(n_steps))
 
 
 def wilson_action_autograd(links, dims, beta):

@@ -214,13 +214,21 @@ struct Bufs {
   }
 };
 
-enum class Smearing { kStout, kApe };
+enum class Smearing { kStout, kApe, kHyp };
 
-// w: rho (stout) or alpha (APE)
+// w: rho (stout) or alpha (APE); a[3] = (a1, a2, a3) for HYP
+struct SmearArgs {
+  Smearing kind;
+  double w;
+  double a[3];
+};
+
 template <typename R>
-static lq_status backward_impl(Smearing kind, const lq_field* thin, double w, int n, unsigned dirs,
+static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n, unsigned dirs,
                                const lq_field* seed, double beta, lq_field* force, lq_field* grad_out, int every,
                                cudaStream_t s) {
+  const Smearing kind = sa.kind;
+  const double w = sa.w;
   const GeomArgs g = geom_args(thin->geom);
   const long long V = g.V;
   const size_t fb = thin->bytes;
@@ -239,11 +247,18 @@ static lq_status backward_impl(Smearing kind, const lq_field* thin, double w, in
   if ((st = alloc(&w0)) || (st = alloc(&w1)) || (st = alloc(&Ga)) || (st = alloc(&Gb)) || (st = alloc(&Kb))) return st;
   for (int j = every; j < n; j += every)
     if ((st = alloc(&ck[j]))) return st;
+  void* hyp_scratch = nullptr;   // decorated links and their gradients
+  if (kind == Smearing::kHyp && n > 0) {
+    if ((st = scratch_alloc(&hyp_scratch, kHypBwdPlanes * (fb / 4), s, "lq_hyp_backward"))) return st;
+    b.own.push_back(hyp_scratch);
+  }
   TuneChoice tc = stout_default_choice(thin->prec);
   // recomputed fields follow lq_stout_smear's default (FP32 links are re-projected)
   const int reproject = thin->prec == LQ_F32 ? 1 : 0;
   auto run_steps = [&](void* links, int steps) -> lq_status {
     if (kind == Smearing::kApe) return ape_run_steps(links, w1, thin->geom, thin->prec, fb, w, steps, dirs, s);
+    if (kind == Smearing::kHyp)
+      return hyp_run_steps(links, w1, hyp_scratch, thin->geom, thin->prec, fb, sa.a[0], sa.a[1], sa.a[2], steps, s);
     return stout_run_steps(links, w1, thin->geom, thin->prec, w, steps, dirs, reproject, tc, s);
   };
   int nd = 0;
@@ -283,6 +298,12 @@ static lq_status backward_impl(Smearing kind, const lq_field* thin, double w, in
     if (!Uj) {
       if ((st = forward_to(j, w0))) return st;
       Uj = w0;
+    }
+    if (kind == Smearing::kHyp) {
+      if ((st = hyp_backward_step(Uj, Ga, Gb, hyp_scratch, thin->geom, thin->prec, fb, sa.a[0], sa.a[1], sa.a[2], s)))
+        return st;
+      std::swap(Ga, Gb);
+      continue;
     }
     dim3 grid((unsigned)((V + 127) / 128), 4);
     if (kind == Smearing::kApe)
@@ -358,10 +379,10 @@ extern "C" lq_status lq_stout_backward(const lq_field* thin, double rho, int n_s
   const int every = checkpoint_every(opts);
   cudaStream_t s = as_stream(stream);
   if (thin->prec == LQ_F64)
-    return backward_impl<double>(Smearing::kStout, thin, rho, n_steps, dirs_mask, grad_seed, beta, force_out,
-                                 grad_out, every, s);
-  return backward_impl<float>(Smearing::kStout, thin, rho, n_steps, dirs_mask, grad_seed, beta, force_out, grad_out,
-                              every, s);
+    return backward_impl<double>(SmearArgs{Smearing::kStout, rho, {0, 0, 0}}, thin, n_steps, dirs_mask, grad_seed,
+                                 beta, force_out, grad_out, every, s);
+  return backward_impl<float>(SmearArgs{Smearing::kStout, rho, {0, 0, 0}}, thin, n_steps, dirs_mask, grad_seed, beta,
+                              force_out, grad_out, every, s);
 }
 
 extern "C" lq_status lq_ape_backward(const lq_field* thin, double alpha, int n_steps, unsigned dirs_mask,
@@ -377,8 +398,28 @@ extern "C" lq_status lq_ape_backward(const lq_field* thin, double alpha, int n_s
   const int every = checkpoint_every(opts);
   cudaStream_t s = as_stream(stream);
   if (thin->prec == LQ_F64)
-    return backward_impl<double>(Smearing::kApe, thin, alpha, n_steps, dirs_mask, grad_seed, beta, force_out,
-                                 grad_out, every, s);
-  return backward_impl<float>(Smearing::kApe, thin, alpha, n_steps, dirs_mask, grad_seed, beta, force_out, grad_out,
-                              every, s);
+    return backward_impl<double>(SmearArgs{Smearing::kApe, alpha, {0, 0, 0}}, thin, n_steps, dirs_mask, grad_seed,
+                                 beta, force_out, grad_out, every, s);
+  return backward_impl<float>(SmearArgs{Smearing::kApe, alpha, {0, 0, 0}}, thin, n_steps, dirs_mask, grad_seed, beta,
+                              force_out, grad_out, every, s);
+}
+
+extern "C" lq_status lq_hyp_backward(const lq_field* thin, double a1, double a2, double a3, int n_steps,
+                                     const lq_field* grad_seed, double beta, lq_field* force_out, lq_field* grad_out,
+                                     const lq_backward_opts* opts, void* stream) {
+  clear_error();
+  lq_status st = check_backward("lq_hyp_backward", thin, 15u, n_steps, beta, grad_seed, force_out, grad_out);
+  if (st != LQ_OK) return st;
+  const double as[3] = {a1, a2, a3};
+  for (double a : as)
+    if (!(a == a) || a > 1e6 || a < -1e6) {
+      set_error("lq_hyp_backward: the weights must be finite");
+      return LQ_ERR_ARG;
+    }
+  const int every = checkpoint_every(opts);
+  cudaStream_t s = as_stream(stream);
+  const SmearArgs sa{Smearing::kHyp, 0.0, {a1, a2, a3}};
+  if (thin->prec == LQ_F64)
+    return backward_impl<double>(sa, thin, n_steps, 15u, grad_seed, beta, force_out, grad_out, every, s);
+  return backward_impl<float>(sa, thin, n_steps, 15u, grad_seed, beta, force_out, grad_out, every, s);
 }

@@ -104,6 +104,14 @@ TuneChoice stout_default_choice(int prec);
 // scratch field of the same size; the arithmetic of lq_ape_smear.
 lq_status ape_run_steps(void* links, void* work, const lq_geom& g, int prec, size_t bytes, double alpha,
                         int n_steps, unsigned dirs, cudaStream_t s);
+// n HYP steps in place; scratch holds 24 colour-matrix planes (bytes / 4 each).
+lq_status hyp_run_steps(void* links, void* work, void* scratch, const lq_geom& g, int prec, size_t bytes,
+                        double a1, double a2, double a3, int n_steps, cudaStream_t s);
+// Gradient through one HYP step: Gout = G at U^(k) from Gp = G at U^(k+1);
+// scratch holds kHypBwdPlanes colour-matrix planes.
+constexpr int kHypBwdPlanes = 64;
+lq_status hyp_backward_step(const void* Uk, const void* Gp, void* Gout, void* scratch, const lq_geom& g, int prec,
+                            size_t bytes, double a1, double a2, double a3, cudaStream_t s);
 // One stout step over the sites [s_begin, s_end) only (global-load kernel).
 lq_status stout_step_range(const void* in, void* out, const lq_geom& g, int prec, double rho, unsigned dirs,
                            int reproject, const TuneChoice& tc, long long s_begin, long long s_end,
