@@ -47,6 +47,11 @@ def _events(torch, fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def _dims(args, default):
+    """--dims Lx,Ly,Lz,Lt overrides a workload's lattice (smaller profiling cases)."""
+    return tuple(int(x) for x in args.dims.split(",")) if args.dims else default
+
+
 def _field(lq, fieldgen, dims, seed, prec, device="cuda"):
     import torch
     U = fieldgen.near_identity_su3_torch(dims, seed, device=device).cpu().numpy()
@@ -96,11 +101,11 @@ FORCE_FLOPS = 198 + 30
 
 def backward24(args, torch, lq, fieldgen):
     import bench
-    dims = (24, 24, 24, 48)
+    dims = _dims(args, (24, 24, 24, 48))
     V = int(np.prod(dims))
     n, rho = 3, 0.1
     out = {"metric": "stout force link-updates/s (3 steps, Wilson action)", "unit": "link-updates/s",
-           "config": {"workload": "24^3x48, exp(i*0.3*H) links seed 4, 3 stout steps rho=0.1 in 4 dims, beta=6"}}
+           "config": {"workload": f"{'x'.join(map(str, dims))}, exp(i*0.3*H) links seed 4, 3 stout steps rho=0.1 in 4 dims, beta=6"}}
     pk = bench.peaks()
     for name, prec in (("f64", lq.LQ_F64), ("f32", lq.LQ_F32)):
         f, _ = _field(lq, fieldgen, dims, 4, prec)
@@ -267,11 +272,11 @@ APE_VJP_FLOPS = 90 + 90 + 210 + 8 + 180 + 12 + 210 + 216 + 396 + 612 + 84 + 432 
 
 def apeforce24(args, torch, lq, fieldgen):
     import bench
-    dims = (24, 24, 24, 48)
+    dims = _dims(args, (24, 24, 24, 48))
     V = int(np.prod(dims))
     n, alpha = 3, 0.6
     out = {"metric": "APE force link-updates/s (3 steps, Wilson action)", "unit": "link-updates/s",
-           "config": {"workload": "24^3x48, exp(i*0.3*H) links seed 4, 3 APE steps alpha=0.6 in 4 dims, beta=6"}}
+           "config": {"workload": f"{'x'.join(map(str, dims))}, exp(i*0.3*H) links seed 4, 3 APE steps alpha=0.6 in 4 dims, beta=6"}}
     mhz = 2070.0
     p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
     p32 = 2.0 * bench.FP32_FMA_PER_CLK * mhz * 1e6
@@ -323,10 +328,10 @@ HYPF_F64_FLOPS_PER_SITE = 80 * APE_PROJECTION_FLOPS + 28 * APE_VJP_FLOPS
 
 def hypforce24(args, torch, lq, fieldgen):
     import bench
-    dims, n, w = (24, 24, 24, 48), 2, (0.75, 0.6, 0.3)
+    dims, n, w = _dims(args, (24, 24, 24, 48)), 2, (0.75, 0.6, 0.3)
     V = int(np.prod(dims))
     out = {"metric": "HYP force link-updates/s (2 steps, Wilson action)", "unit": "link-updates/s",
-           "config": {"workload": "24^3x48, exp(i*0.3*H) links seed 4, 2 HYP steps (0.75, 0.6, 0.3), beta=6"}}
+           "config": {"workload": f"{'x'.join(map(str, dims))}, exp(i*0.3*H) links seed 4, 2 HYP steps (0.75, 0.6, 0.3), beta=6"}}
     mhz = 2070.0
     p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
     for name, prec in (("f64", lq.LQ_F64), ("f32", lq.LQ_F32)):
