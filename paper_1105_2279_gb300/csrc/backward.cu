@@ -142,14 +142,16 @@ __device__ __forceinline__ M3<R> ld(const V2<R>* __restrict__ F, long long V, in
 //                 + K_mu(y-mu)^dag U_a(y-mu) U_mu(y-mu+a) + U_mu(y) U_a(y+mu) K_mu(y+a)^dag
 //                 + U_mu(y-mu)^dag U_a(y-mu) K_mu(y-mu+a)
 //                 + U_mu(y-mu)^dag K_a(y-mu) U_mu(y-mu+a) + U_mu(y) K_a(y+mu) U_mu(y+a)^dag ]
+// The four directions of a block of sites run in consecutive CTAs, so the
+// neighbour links and K they share are read while still in L2.
 template <typename R>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_bwd_staple(const V2<R>* __restrict__ U, const V2<R>* __restrict__ K,
                                                     V2<R>* __restrict__ G, GeomArgs g, unsigned dirs) {
   const long long V = g.V;
-  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long sl = (long long)(blockIdx.x / 4) * blockDim.x + threadIdx.x;
   if (sl >= V) return;
   const int s = (int)sl;
-  const int a = blockIdx.y;
+  const int a = blockIdx.x % 4;
   if (!((dirs >> a) & 1u)) return;
   int c[4];
   site_coords(g, s, c);
@@ -312,7 +314,7 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
     else
       k_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g, (R)w, dirs);
     if ((st = launch_check("backward link kernel"))) return st;
-    k_bwd_staple<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Kb, (V2<R>*)Gb, g, dirs);
+    k_bwd_staple<R><<<grid.x * 4, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Kb, (V2<R>*)Gb, g, dirs);
     if ((st = launch_check("k_bwd_staple"))) return st;
     std::swap(Ga, Gb);
   }

@@ -360,7 +360,9 @@ __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, d
   const double re3 = p.re * o02.re + p.im * o02.im;
   const double c0 = d0 * d1 * d2 - d0 * n12 - d1 * n02 - d2 * n01 + 2.0 * re3;
   if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {
-    expiq_series_deriv<10>(c0, c1, series_order<2>(c1) + 1, r.f, r.b1, r.b2);
+    // the order of the f_j's series for the link precision (tol 1e-13 on FP32
+    // links, 1e-17 on FP64), plus one
+    expiq_series_deriv<10>(c0, c1, series_order<NR == 1 ? 1 : 2>(c1) + 1, r.f, r.b1, r.b2);
     return r;
   }
   if (!(c1 >= LQ_C1_SERIES)) {  // NaN (small c1 took the series)
