@@ -116,7 +116,9 @@ def backward24(args, torch, lq, fieldgen):
         stats64 = lq.stout_ch_stats(g64, rho, n, (0, 1, 2, 3))
         del g64
         mean_k = stats64[2] / max(1, stats64[1])
-        ch_deriv = 35 + 48 + 24 * (2 * mean_k + 4)
+        # the derivative series runs at the links' own table order plus one
+        own_k = stats[2] / max(1, stats[1])
+        ch_deriv = 35 + 48 + 24 * (2 * own_k + 4)
         fwd_f64 = bench.ch_flops_per_link(stats) + (bench.REPROJECT_FLOPS_PER_LINK if prec == lq.LQ_F32
                                                      else bench.MATRIX_FLOPS_PER_LINK)
         algebra = n * (BWD_LOCAL_FLOPS + BWD_GATHER_FLOPS) + WILSON_GRAD_FLOPS + FORCE_FLOPS
@@ -138,7 +140,7 @@ def backward24(args, torch, lq, fieldgen):
                            "frac": flops64 * 4 * V / t1 / p64,
                            "t_bound_ms": {"fp64": 1e3 * flops64 * 4 * V / p64, "fp32": 1e3 * flops32 * 4 * V / p32},
                            "peak_source": f"derived: {bench.FP64_FMA_PER_CLK} FP64 FMA/clk x 2 x {mhz:.0f} MHz",
-                           "mean_series_order_fp64_table": mean_k,
+                           "mean_series_order_fp64_table": mean_k, "mean_series_order_own_table": own_k,
                            "note": "checkpoint_every=1; flops of the forward recompute included"}
         g = lq.Field(f.geom, lq.LQ_LINKS, prec)
         g.tensor.copy_(f.tensor)

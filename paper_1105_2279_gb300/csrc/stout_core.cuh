@@ -544,6 +544,88 @@ template <typename R> __device__ __forceinline__ M3<R> reproject_via_f64(const M
   return r;
 }
 
+// The FP64 re-projection of an FP32 link, arranged so that the FP64 pipe does
+// only the cancellation-prone part.  Rows u0, u1 of the FP32 link are exact
+// in FP64 and so are the products of their entries; Gram-Schmidt gives
+//   r0 = n0 u0,  r1 = n1 (u1 - c u0),  r2 = conj(r0 x r1),
+//   n0 = (1 + d0)^(-1/2),  d0 = |u0|^2 - 1,  p = u0^dag u1,  c = n0^2 p,
+//   n1 = (1 + d1)^(-1/2),  d1 = |u1|^2 - 1 - n0^2 |p|^2.
+// d0, |u1|^2 - 1 and p (sums that cancel to ~1e-7) and the cross product
+// u0 x u1 (entries that can be small) are formed in FP64.  For a link unitary
+// to FP32 rounding the rest are corrections of relative size <= 2^-16
+// (checked; otherwise the Gram-Schmidt of reproject_f64 runs on the whole
+// link), so their FP32 rounding (6e-8 of a correction) stays below 1e-12:
+//   row 0  = u0 + e0 u0,           e0 = n0 - 1 = -d0/2 + 3 d0^2/8
+//   row 1  = u1 + a1,              a1 = e1 u1 - c n1 u0,  e1 = n1 - 1
+//   r0 x r1 = u0 x u1 + e0 (u0 x u1) + n0 (u0 x a1)   (products of two corrections dropped)
+// each row rounded to FP32 once, the FP32 correction of row 2 folded into the
+// accumulator of its FP64 cross product.  The result is the FP64 Gram-Schmidt
+// rounded to FP32 except where the exact value lies within ~1e-12 of a
+// rounding boundary; 48 FP64 instructions against 76.
+__device__ __noinline__ M3<float> reproject_f32_general(M3<float> m) {
+  M3<double> d;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d.e[i] = mkc(to_f64(m.e[i].re), to_f64(m.e[i].im));
+  reproject_f64<1>(d);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) m.e[i] = mkc<float>(from_f64<float>(d.e[i].re), from_f64<float>(d.e[i].im));
+  return m;
+}
+
+__device__ __forceinline__ M3<float> reproject_f32(const M3<float>& m) {
+  cx<double> r[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r[i] = mkc(to_f64(m.e[i].re), to_f64(m.e[i].im));
+  const double d0 = row_norm2_m1(&r[0]);
+  const double d1b = row_norm2_m1(&r[3]);
+  cx<double> p = mkc(r[0].re * r[3].re, r[0].re * r[3].im);   // sum_k conj(u0_k) u1_k
+  p.re = fma(r[0].im, r[3].im, p.re);
+  p.im = fma(-r[0].im, r[3].re, p.im);
+  p = cfma_cn(r[1], r[4], p);
+  p = cfma_cn(r[2], r[5], p);
+  const float d0f = to_f32(d0), d1bf = to_f32(d1b);
+  const cx<float> pf = mkc(to_f32(p.re), to_f32(p.im));
+  const float lim = 1.52587890625e-05f;   // 2^-16
+  if (!(fabsf(d0f) <= lim && fabsf(d1bf) <= lim && fabsf(pf.re) + fabsf(pf.im) <= lim))
+    return reproject_f32_general(m);
+  const float e0 = d0f * fmaf(d0f, 0.375f, -0.5f);
+  const float n0sq = fmaf(2.0f, e0, 1.0f);                    // (1 + e0)^2 up to e0^2
+  const float d1f = fmaf(-n0sq, fmaf(pf.re, pf.re, pf.im * pf.im), d1bf);
+  const float e1 = d1f * fmaf(d1f, 0.375f, -0.5f);
+  const float cs = n0sq * (1.0f + e1);                         // c n1 = n0^2 n1 p
+  const cx<float> cn = mkc(pf.re * cs, pf.im * cs);
+  M3<float> out;
+  cx<float> a1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const cx<float> u0 = m.e[k], u1 = m.e[3 + k];
+    out.e[k] = mkc(fmaf(u0.re, e0, u0.re), fmaf(u0.im, e0, u0.im));
+    // a1 = e1 u1 - cn u0
+    a1[k] = mkc(fmaf(-cn.re, u0.re, fmaf(cn.im, u0.im, e1 * u1.re)),
+                fmaf(-cn.re, u0.im, fmaf(-cn.im, u0.re, e1 * u1.im)));
+    out.e[3 + k] = mkc(u1.re + a1[k].re, u1.im + a1[k].im);
+  }
+  const float n0 = 1.0f + e0;
+  // component j of r0 x r1: (i, l) the two other indices, r0_i r1_l - r0_l r1_i
+  auto row2 = [&](int i, int l) {
+    const cx<float> u0i = m.e[i], u0l = m.e[l], u1i = m.e[3 + i], u1l = m.e[3 + l];
+    const cx<float> x = csub(cmul(u0i, u1l), cmul(u0l, u1i));             // u0 x u1 (FP32 copy)
+    const cx<float> y = csub(cmul(u0i, a1[l]), cmul(u0l, a1[i]));         // u0 x a1
+    const cx<float> corr = mkc(fmaf(e0, x.re, n0 * y.re), fmaf(e0, x.im, n0 * y.im));
+    // FP64: u0_i u1_l - (u0_l u1_i - corr)
+    const cx<double> t = cfma(r[l], r[3 + i], mkc(-to_f64(corr.re), -to_f64(corr.im)));
+    const cx<double> v = cfma(r[i], r[3 + l], mkc(-t.re, -t.im));
+    return mkc(to_f32(v.re), -to_f32(v.im));
+  };
+  out.e[6] = row2(1, 2);
+  out.e[7] = row2(2, 0);
+  out.e[8] = row2(0, 1);
+  return out;
+}
+
+template <typename R> __device__ __forceinline__ M3<R> reproject_link(const M3<R>& m) { return reproject_via_f64(m); }
+template <> __device__ __forceinline__ M3<float> reproject_link<float>(const M3<float>& m) { return reproject_f32(m); }
+
 // New link from the bare staple sum S and U_mu(x): FP64 coefficients always;
 // matrix algebra in R; optional FP64 re-projection.
 template <typename R>
@@ -561,7 +643,7 @@ __device__ __forceinline__ M3<R> stout_update(const M3<R>& S, const M3<R>& Umu, 
                                  mkc<R>(from_f64<R>(f.f1.re), from_f64<R>(f.f1.im)),
                                  mkc<R>(from_f64<R>(f.f2.re), from_f64<R>(f.f2.im)));
   M3<R> Up = mul_nn(E, Umu);
-  if (reproject) Up = reproject_via_f64(Up);
+  if (reproject) Up = reproject_link<R>(Up);
   if (korder) *korder = f.k;
   return Up;
 }

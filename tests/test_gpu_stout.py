@@ -262,6 +262,33 @@ def test_reprojection(gpu, prec, scale):
         assert np.max(np.abs(got - plain)) < (1e-6 if prec == lq.LQ_F32 else 1e-14)
 
 
+def _gram_schmidt_f64(u):
+    """FP64 Gram-Schmidt of rows 0 and 1, row 2 = conj(r0 x r1), of complex64 links."""
+    m = u.astype(np.complex128)
+    r0 = m[..., 0, :] / np.sqrt(np.sum(np.abs(m[..., 0, :]) ** 2, axis=-1))[..., None]
+    r1 = m[..., 1, :] - np.sum(np.conj(r0) * m[..., 1, :], axis=-1)[..., None] * r0
+    r1 = r1 / np.sqrt(np.sum(np.abs(r1) ** 2, axis=-1))[..., None]
+    return np.stack([r0, r1, np.conj(np.cross(r0, r1))], axis=-2)
+
+
+@pytest.mark.parametrize("gen,rho", [("near", 0.1), ("haar", 0.25)])
+def test_fp32_reprojection_is_the_fp64_gram_schmidt(gpu, gen, rho):
+    """One FP32 step with and without the re-projection: the re-projected links
+    are the FP64 Gram-Schmidt of the others rounded to FP32, except elements
+    whose exact value lies within ~1e-12 of an FP32 rounding boundary (the
+    kernel applies the small corrections in FP32), which may differ by one
+    unit in the last place."""
+    dims = (8, 8, 8, 8)
+    U = fieldgen.haar_su3(dims, 712) if gen == "haar" else fieldgen.near_identity_su3(dims, 712)
+    plain = _run(U, lq.LQ_F32, rho, 1, ALL, reproject=False)
+    got = _run(U, lq.LQ_F32, rho, 1, ALL, reproject=True)
+    ref = _gram_schmidt_f64(plain).astype(np.complex64)
+    differ = np.count_nonzero(got != ref)
+    assert differ <= 1e-4 * got.size, differ
+    ulp = np.spacing(np.maximum(np.abs(ref.real), np.abs(ref.imag)).astype(np.float32))
+    assert np.all(np.abs(got.real - ref.real) <= ulp) and np.all(np.abs(got.imag - ref.imag) <= ulp)
+
+
 @pytest.mark.parametrize("dims,gen,rho,n,dirs", [
     ((4, 4, 4, 4), "haar", 0.1, 1, ALL),
     ((3, 4, 5, 6), "near", 0.125, 3, ALL),
