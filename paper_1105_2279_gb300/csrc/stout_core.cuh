@@ -562,7 +562,7 @@ template <typename R> __device__ __forceinline__ M3<R> reproject_via_f64(const M
 // accumulator of its FP64 cross product.  The result is the FP64 Gram-Schmidt
 // rounded to FP32 except where the exact value lies within ~1e-12 of a
 // rounding boundary; 48 FP64 instructions against 76.
-__device__ __noinline__ M3<float> reproject_f32_general(M3<float> m) {
+static __device__ __noinline__ M3<float> reproject_f32_general(M3<float> m) {
   M3<double> d;
 #pragma unroll
   for (int i = 0; i < 6; ++i) d.e[i] = mkc(to_f64(m.e[i].re), to_f64(m.e[i].im));
