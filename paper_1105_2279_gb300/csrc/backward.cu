@@ -231,13 +231,15 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
                                cudaStream_t s) {
   const Smearing kind = sa.kind;
   const double w = sa.w;
+  const char* who = kind == Smearing::kStout ? "lq_stout_backward"
+                                             : (kind == Smearing::kApe ? "lq_ape_backward" : "lq_hyp_backward");
   const GeomArgs g = geom_args(thin->geom);
   const long long V = g.V;
   const size_t fb = thin->bytes;
   Bufs b;
   b.s = s;
   auto alloc = [&](void** p) -> lq_status {
-    lq_status st = scratch_alloc(p, fb, s, "lq_stout_backward");
+    lq_status st = scratch_alloc(p, fb, s, who);
     if (st == LQ_OK) b.own.push_back(*p);
     return st;
   };
@@ -245,13 +247,14 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
   // checkpoints: ck[j] holds U^(j) for j % every == 0 (ck[0] is the thin field itself)
   std::vector<void*> ck(n + 1, nullptr);
   ck[0] = thin->ptr;
-  void *w0, *w1, *Ga, *Gb, *Kb;
-  if ((st = alloc(&w0)) || (st = alloc(&w1)) || (st = alloc(&Ga)) || (st = alloc(&Gb)) || (st = alloc(&Kb))) return st;
+  void *w0, *w1, *Ga, *Gb, *Kb = nullptr;   // Kb: staple-sum gradient (stout and APE only)
+  if ((st = alloc(&w0)) || (st = alloc(&w1)) || (st = alloc(&Ga)) || (st = alloc(&Gb))) return st;
+  if (kind != Smearing::kHyp && (st = alloc(&Kb))) return st;
   for (int j = every; j < n; j += every)
     if ((st = alloc(&ck[j]))) return st;
   void* hyp_scratch = nullptr;   // decorated links and their gradients
   if (kind == Smearing::kHyp && n > 0) {
-    if ((st = scratch_alloc(&hyp_scratch, kHypBwdPlanes * (fb / 4), s, "lq_hyp_backward"))) return st;
+    if ((st = scratch_alloc(&hyp_scratch, kHypBwdPlanes * (fb / 4), s, who))) return st;
     b.own.push_back(hyp_scratch);
   }
   TuneChoice tc = stout_default_choice(thin->prec);
@@ -271,19 +274,18 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
   auto forward_to = [&](int j, void* dst) -> lq_status {
     int j0 = (j / every) * every;
     if (j0 >= n) j0 = ((n - 1) / every) * every;
-    lq_status st2 = cuda_check(cudaMemcpyAsync(dst, ck[j0], fb, cudaMemcpyDeviceToDevice, s), "lq_stout_backward copy");
+    lq_status st2 = cuda_check(cudaMemcpyAsync(dst, ck[j0], fb, cudaMemcpyDeviceToDevice, s), who);
     if (st2 != LQ_OK) return st2;
     return run_steps(dst, j - j0);
   };
   for (int j = every; j < n; j += every) {  // ck[j] = `every` steps from ck[j - every]
-    if ((st = cuda_check(cudaMemcpyAsync(ck[j], ck[j - every], fb, cudaMemcpyDeviceToDevice, s),
-                         "lq_stout_backward checkpoint")))
+    if ((st = cuda_check(cudaMemcpyAsync(ck[j], ck[j - every], fb, cudaMemcpyDeviceToDevice, s), who)))
       return st;
     if ((st = run_steps(ck[j], every))) return st;
   }
   // seed at U^(n)
   if (seed) {
-    if ((st = cuda_check(cudaMemcpyAsync(Ga, seed->ptr, fb, cudaMemcpyDeviceToDevice, s), "lq_stout_backward seed")))
+    if ((st = cuda_check(cudaMemcpyAsync(Ga, seed->ptr, fb, cudaMemcpyDeviceToDevice, s), who)))
       return st;
   } else {
     void* Un = thin->ptr;
@@ -324,7 +326,7 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
     if ((st = launch_check("k_force"))) return st;
   }
   if (grad_out)
-    if ((st = cuda_check(cudaMemcpyAsync(grad_out->ptr, Ga, fb, cudaMemcpyDeviceToDevice, s), "lq_stout_backward grad")))
+    if ((st = cuda_check(cudaMemcpyAsync(grad_out->ptr, Ga, fb, cudaMemcpyDeviceToDevice, s), who)))
       return st;
   return LQ_OK;
 }

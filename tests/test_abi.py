@@ -117,7 +117,18 @@ def test_injected_allocation_failure_is_reported(lqlib, monkeypatch):
     out = (ctypes.c_double * 3)()
     assert lib.lq_plaquette(h, out, None) == -3
     assert lib.lq_stout_backward(h, 0.1, 1, 15, None, 6.0, h, None, None, None) in (-1, -3)
+    # the APE and HYP smearings and forces allocate their scratch before any launch
+    f = ctypes.c_void_p()
+    assert lib.lq_field_wrap(g.handle, 0, 1, ctypes.c_void_p(0x2000), need, ctypes.byref(f)) == 0
+    assert lib.lq_ape_smear(h, 0.5, 1, 15, None) == -3
+    assert lib.lq_hyp_smear(h, 0.75, 0.6, 0.3, 1, None) == -3
+    for call in (lambda: lib.lq_stout_backward(h, 0.1, 1, 15, None, 6.0, f, None, None, None),
+                 lambda: lib.lq_ape_backward(h, 0.6, 1, 15, None, 6.0, f, None, None, None),
+                 lambda: lib.lq_hyp_backward(h, 0.75, 0.6, 0.3, 1, None, 6.0, f, None, None, None)):
+        assert call() == -3
+        assert b"fault injected" in lib.lq_last_error()
     monkeypatch.delenv("LQ_FAULT_INJECT")
+    lib.lq_field_free(f)
     lib.lq_field_free(h)
 
 
