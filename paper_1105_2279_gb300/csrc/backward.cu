@@ -36,50 +36,9 @@ template <typename R> __device__ __forceinline__ cx<R> tr_dn(const M3<R>& a, con
   return t;
 }
 
-template <typename R> __device__ __forceinline__ CHDeriv bwd_coefficients(const QH<R>& q) {
-  return ch_coefficients_deriv<sizeof(R) == 4 ? 1 : 2>(
-      to_f64(q.d0), to_f64(q.d1), to_f64(q.d2), mkc(to_f64(q.o01.re), to_f64(q.o01.im)),
-      mkc(to_f64(q.o02.re), to_f64(q.o02.im)), mkc(to_f64(q.o12.re), to_f64(q.o12.im)));
-}
-
-// The coefficient stage of one step on its own (FP32 links): f_j, b1_j, b2_j
-// of every smeared link as 18 FP64 planes [k][mu][site] (k = 2j + re/im for
-// f, 6 + .. for b1, 12 + .. for b2).  It depends on U^(j) only, so it runs
-// on a side stream beside the FP32 kernels of the step after it.
-constexpr int kCoefPlanes = 18;
-
 template <typename R>
-__global__ void __launch_bounds__(128) k_bwd_coef(const V2<R>* __restrict__ U, double* __restrict__ coef, GeomArgs g,
-                                                  R rho, unsigned dirs) {
-  const long long V = g.V;
-  const long long sl = (long long)(blockIdx.x / 4) * blockDim.x + threadIdx.x;
-  if (sl >= V) return;
-  const int s = (int)sl;
-  const int mu = blockIdx.x % 4;
-  if (!((dirs >> mu) & 1u)) return;
-  int c[4];
-  site_coords(g, s, c);
-  const long long off = (long long)mu * 9 * V + s;
-  const M3<R> C = m_rscale(staple_sum<R>(U, g, s, c, mu, dirs), rho);
-  const CHDeriv d = bwd_coefficients<R>(q_from_omega(mul_nd(C, ld_m3<R>(U + off, V))));
-  double* o = coef + (long long)mu * V + s;
-  const long long ps = 4 * V;   // plane stride
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    o[(2 * j) * ps] = d.f[j].re;
-    o[(2 * j + 1) * ps] = d.f[j].im;
-    o[(6 + 2 * j) * ps] = d.b1[j].re;
-    o[(7 + 2 * j) * ps] = d.b1[j].im;
-    o[(12 + 2 * j) * ps] = d.b2[j].re;
-    o[(13 + 2 * j) * ps] = d.b2[j].im;
-  }
-}
-
-// PRE: the coefficients come from k_bwd_coef's planes instead of being formed here.
-template <typename R, bool PRE>
 __global__ void __launch_bounds__(128) k_bwd_link(const V2<R>* __restrict__ U, const V2<R>* __restrict__ Gp,
-                                                  V2<R>* __restrict__ Gout, V2<R>* __restrict__ K,
-                                                  const double* __restrict__ coef, GeomArgs g, R rho,
+                                                  V2<R>* __restrict__ Gout, V2<R>* __restrict__ K, GeomArgs g, R rho,
                                                   unsigned dirs) {
   const long long V = g.V;
   const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,19 +55,9 @@ __global__ void __launch_bounds__(128) k_bwd_link(const V2<R>* __restrict__ U, c
   const M3<R> C = m_rscale(staple_sum<R>(U, g, s, c, mu, dirs), rho);
   const M3<R> Umu = ld_m3<R>(U + off, V);
   const QH<R> q = q_from_omega(mul_nd(C, Umu));
-  CHDeriv d;
-  if (PRE) {
-    const double* o = coef + (long long)mu * V + s;
-    const long long ps = 4 * V;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      d.f[j] = mkc(o[(2 * j) * ps], o[(2 * j + 1) * ps]);
-      d.b1[j] = mkc(o[(6 + 2 * j) * ps], o[(7 + 2 * j) * ps]);
-      d.b2[j] = mkc(o[(12 + 2 * j) * ps], o[(13 + 2 * j) * ps]);
-    }
-  } else {
-    d = bwd_coefficients<R>(q);
-  }
+  const CHDeriv d = ch_coefficients_deriv<sizeof(R) == 4 ? 1 : 2>(
+      to_f64(q.d0), to_f64(q.d1), to_f64(q.d2), mkc(to_f64(q.o01.re), to_f64(q.o01.im)),
+      mkc(to_f64(q.o02.re), to_f64(q.o02.im)), mkc(to_f64(q.o12.re), to_f64(q.o12.im)));
   const QH<R> q2 = q_square(q);
   const M3<R> Qf = qh_full(q), Q2f = qh_full(q2);
   const M3<R> Gpm = ld_m3<R>(Gp + off, V);
@@ -267,44 +216,6 @@ struct Bufs {
   }
 };
 
-// A non-blocking side stream that starts after the work queued so far on s,
-// with two "coefficients ready" and two "buffer free" events (the latter
-// recorded once up front, so the first waits pass).  On destruction s waits
-// for everything queued on the side stream (so stream-ordered frees on s that
-// follow cannot overtake it, also on an error return), then the stream and
-// the events are released (allowed with work pending).
-struct SideStream {
-  cudaStream_t stream = nullptr, main = nullptr;
-  cudaEvent_t ready[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
-  lq_status open(cudaStream_t s) {
-    main = s;
-    lq_status st = cuda_check(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "side stream");
-    for (int r = 0; r < 2 && st == LQ_OK; ++r) {
-      st = cuda_check(cudaEventCreateWithFlags(&ready[r], cudaEventDisableTiming), "side stream event");
-      if (st == LQ_OK) st = cuda_check(cudaEventCreateWithFlags(&freed[r], cudaEventDisableTiming), "side stream event");
-      if (st == LQ_OK) st = cuda_check(cudaEventRecord(freed[r], s), "side stream event");
-    }
-    if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(stream, freed[0], 0), "side stream start");
-    return st;
-  }
-  ~SideStream() {
-    if (stream) {
-      cudaEvent_t done = nullptr;
-      if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
-        if (cudaEventRecord(done, stream) == cudaSuccess) cudaStreamWaitEvent(main, done, 0);
-        cudaEventDestroy(done);
-      } else {
-        cudaStreamSynchronize(stream);
-      }
-    }
-    for (int r = 0; r < 2; ++r) {
-      if (ready[r]) cudaEventDestroy(ready[r]);
-      if (freed[r]) cudaEventDestroy(freed[r]);
-    }
-    if (stream) cudaStreamDestroy(stream);
-  }
-};
-
 enum class Smearing { kStout, kApe, kHyp };
 
 // w: rho (stout) or alpha (APE); a[3] = (a1, a2, a3) for HYP
@@ -386,36 +297,12 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
     k_wilson_grad<R><<<grid, 128, 0, s>>>((const V2<R>*)Un, (V2<R>*)Ga, g, (R)(-beta / 3.0));
     if ((st = launch_check("k_wilson_grad"))) return st;
   }
-  // FP32 stout links with every step kept: the FP64 coefficient stage of
-  // step j - 1 runs on a side stream while step j's FP32 kernels run, into a
-  // ring of two coefficient buffers (events: coefficients ready, buffer free)
-  const bool side = kind == Smearing::kStout && sizeof(R) == 4 && every == 1 && n > 0;
-  SideStream ss;
-  double* cbuf[2] = {nullptr, nullptr};
-  if (side) {
-    const size_t cb = (size_t)kCoefPlanes * 4 * (size_t)V * sizeof(double);
-    for (int r = 0; r < 2; ++r) {
-      if ((st = scratch_alloc((void**)&cbuf[r], cb, s, who))) return st;
-      b.own.push_back(cbuf[r]);
-    }
-    if ((st = ss.open(s))) return st;
-  }
-  auto launch_coef = [&](int j) -> lq_status {   // on the side stream, into cbuf[j % 2]
-    lq_status st2 = cuda_check(cudaStreamWaitEvent(ss.stream, ss.freed[j % 2], 0), who);
-    if (st2 != LQ_OK) return st2;
-    k_bwd_coef<R><<<(unsigned)((V + 127) / 128) * 4, 128, 0, ss.stream>>>((const V2<R>*)ck[j], cbuf[j % 2], g,
-                                                                          (R)w, dirs);
-    if ((st2 = launch_check("k_bwd_coef"))) return st2;
-    return cuda_check(cudaEventRecord(ss.ready[j % 2], ss.stream), who);
-  };
-  if (side && (st = launch_coef(n - 1))) return st;
   for (int j = n - 1; j >= 0; --j) {
     const void* Uj = ck[j];
     if (!Uj) {
       if ((st = forward_to(j, w0))) return st;
       Uj = w0;
     }
-    if (side && j > 0 && (st = launch_coef(j - 1))) return st;   // overlaps step j below
     if (kind == Smearing::kHyp) {
       if ((st = hyp_backward_step(Uj, Ga, Gb, hyp_scratch, thin->geom, thin->prec, fb, sa.a[0], sa.a[1], sa.a[2], s)))
         return st;
@@ -426,15 +313,8 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
     if (kind == Smearing::kApe)
       k_ape_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g,
                                              (R)(1.0 - w), (R)ape_coef, dirs);
-    else if (side) {
-      if ((st = cuda_check(cudaStreamWaitEvent(s, ss.ready[j % 2], 0), who))) return st;
-      k_bwd_link<R, true><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb,
-                                               cbuf[j % 2], g, (R)w, dirs);
-      if ((st = launch_check("backward link kernel"))) return st;
-      if ((st = cuda_check(cudaEventRecord(ss.freed[j % 2], s), who))) return st;
-    } else
-      k_bwd_link<R, false><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb,
-                                                nullptr, g, (R)w, dirs);
+    else
+      k_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g, (R)w, dirs);
     if ((st = launch_check("backward link kernel"))) return st;
     k_bwd_staple<R><<<grid.x * 4, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Kb, (V2<R>*)Gb, g, dirs);
     if ((st = launch_check("k_bwd_staple"))) return st;

@@ -67,19 +67,6 @@ def test_force_smooth_fields(gpu, eps):
     assert np.max(np.abs(G - G_ref)) <= 1e-12 * np.max(np.abs(G_ref))
 
 
-def test_f32_side_stream_coefficients_match_the_fused_kernel(gpu):
-    """FP32 links with every step kept run the coefficient stage on a side
-    stream (k_bwd_coef) beside the previous step's FP32 kernels; recomputing
-    from every third step runs it inside the link kernel.  Same arithmetic,
-    so the two agree to FP32 rounding of identical operations."""
-    dims = (4, 3, 4, 3)
-    U = fieldgen.near_identity_su3(dims, 306)
-    F1, G1 = gpu_force(U, lq.LQ_F32, 0.1, 4, ALL, every=1)
-    F3, G3 = gpu_force(U, lq.LQ_F32, 0.1, 4, ALL, every=3)
-    assert np.max(np.abs(F1 - F3)) <= 1e-6 * np.max(np.abs(F3))
-    assert np.max(np.abs(G1 - G3)) <= 1e-6 * np.max(np.abs(G3))
-
-
 @pytest.mark.parametrize("n,dirs", [(1, ALL), (2, SPATIAL)])
 def test_force_f32(gpu, n, dirs):
     dims = (4, 3, 4, 3)
