@@ -1,0 +1,97 @@
+"""CPU checks of the algebraic identities the CUDA kernels are built on,
+restated in numpy (FP64): a mistake in a kernel's derivation shows here
+without a GPU; the kernels themselves are checked on the GPU against the
+oracle.
+
+* The closed-form Lyapunov solve of the projection's gradient (APE/HYP
+  forces): for Hermitian positive definite Z with elementary symmetric
+  functions p1, p2, p3 of its eigenvalues, Y = A C + C A - Z C Z
+  - p1 (Z C - C Z) + p2 C with A = Z^2 and C = H (p1 A + p3)^-1 / 2 solves
+  Z Y + Y Z = H.
+* The gradient of the projection assembled from it,
+  G_V = (G_W - 2 W Y) Z^-1 with G_W = conj(z) G_P + (i/3) Im tr(G_P^dag P) W,
+  against the oracle's Daleckii-Krein form.
+* The FP32-link re-projection's split: with d0 = |u0|^2 - 1, p = u0^dag u1,
+  e0 = (1 + d0)^-1/2 - 1, c = (1 + e0)^2 p, d1 = |u1|^2 - 1 - (1 + e0)^2 |p|^2,
+  e1 = (1 + d1)^-1/2 - 1, a1 = e1 u1 - c (1 + e1) u0, the rows u0 + e0 u0,
+  u1 + a1 and conj(u0 x u1 + e0 (u0 x u1) + (1 + e0) (u0 x a1)) are the
+  Gram-Schmidt rows.
+"""
+import numpy as np
+import pytest
+
+import fieldgen
+from oracle import ape, ape_force
+from oracle.su3 import adj
+
+
+def _herm(m):
+    return 0.5 * (m + adj(m))
+
+
+def _lyapunov_closed_form(Z, H):
+    lam = np.linalg.eigvalsh(Z)
+    p1, p2, p3 = lam.sum(), lam[0] * lam[1] + lam[1] * lam[2] + lam[0] * lam[2], lam.prod()
+    A = Z @ Z
+    C = H @ np.linalg.inv(p1 * A + p3 * np.eye(3)) / 2.0
+    return A @ C + C @ A - Z @ C @ Z - p1 * (Z @ C - C @ Z) + p2 * C
+
+
+@pytest.mark.parametrize("spread", [1.0, 1e-6, 10.0])
+def test_lyapunov_closed_form(spread):
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        Q = fieldgen.haar_su3((1, 1, 1, 1), int(rng.integers(1 << 30)))[0, 0, 0, 0, 0]
+        s = 1.0 + spread * rng.uniform(0.0, 1.0, 3)
+        Z = (Q * s) @ adj(Q)
+        H = _herm(rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3)))
+        Y = _lyapunov_closed_form(Z, H)
+        assert np.max(np.abs(Z @ Y + Y @ Z - H)) < 1e-12 * max(1.0, spread)
+
+
+def test_projection_gradient_assembly_matches_daleckii_krein():
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        V = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+        if np.linalg.cond(V) > 10:
+            continue
+        G_P = rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3))
+        P = ape.project_su3(V)
+        A = adj(V) @ V
+        lam, q = np.linalg.eigh(A)
+        Z = (q * np.sqrt(lam)) @ adj(q)
+        X = np.linalg.inv(Z)
+        W = V @ X
+        z = np.exp(-1j * np.angle(np.linalg.det(W)) / 3.0)
+        G_W = np.conj(z) * G_P + (1j / 3.0) * np.imag(np.trace(adj(G_P) @ P)) * W
+        Y = _lyapunov_closed_form(Z, _herm(adj(V) @ G_W))
+        G_V = (G_W - 2.0 * W @ Y) @ X
+        ref = ape_force.project_su3_vjp(V, G_P)
+        assert np.max(np.abs(G_V - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_reprojection_split_is_gram_schmidt():
+    rng = np.random.default_rng(13)
+    U = fieldgen.haar_su3((2, 2, 2, 2), 14).reshape(-1, 3, 3)
+    for u in U:
+        u = u + 1e-6 * (rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3)))
+        u0, u1 = u[0], u[1]
+        # Gram-Schmidt, written out
+        r0 = u0 / np.linalg.norm(u0)
+        r1 = u1 - np.vdot(r0, u1) * r0
+        r1 = r1 / np.linalg.norm(r1)
+        r2 = np.conj(np.cross(r0, r1))
+        # the split
+        d0 = np.vdot(u0, u0).real - 1.0
+        p = np.vdot(u0, u1)
+        e0 = (1.0 + d0) ** -0.5 - 1.0
+        c = (1.0 + e0) ** 2 * p
+        d1 = np.vdot(u1, u1).real - 1.0 - (1.0 + e0) ** 2 * abs(p) ** 2
+        e1 = (1.0 + d1) ** -0.5 - 1.0
+        a1 = e1 * u1 - c * (1.0 + e1) * u0
+        x = np.cross(u0, u1)
+        s0, s1 = u0 + e0 * u0, u1 + a1
+        s2 = np.conj(x + e0 * x + (1.0 + e0) * np.cross(u0, a1))
+        assert np.max(np.abs(s0 - r0)) < 1e-15
+        assert np.max(np.abs(s1 - r1)) < 1e-15
+        assert np.max(np.abs(s2 - r2)) < 1e-15
