@@ -293,8 +293,11 @@ typedef struct lq_backward_opts {
  *   grad_out:  optional LINKS field receiving G w.r.t. the thin links.
  * The recursion is the stout force of [MP] Sec. IV, evaluated with the same
  * precision rules as lq_stout_smear (FP32 links: FP32 matrix algebra, FP64
- * coefficients).  Scratch memory (checkpoints and two gradient fields) is
- * allocated stream-ordered. */
+ * coefficients).  One kernel per step runs the staple gather of step j+1
+ * and the link stage of step j on each link.  Scratch memory is allocated
+ * stream-ordered: the kept checkpoints, two gradient fields, two fields of
+ * the staple-sum gradient, one link field for U^(n) (Wilson seed only) and,
+ * when checkpoint_every > 1, three link fields for the recomputation. */
 lq_status lq_stout_backward(const lq_field* thin_links, double rho, int n_steps, unsigned dirs_mask,
                             const lq_field* grad_seed, double beta, lq_field* force_out,
                             lq_field* grad_out, const lq_backward_opts* opts, void* stream);

@@ -49,16 +49,34 @@ using namespace lq;
 
 namespace lq {
 
-lq_status ape_run_steps(void* links, void* work, const lq_geom& geom, int prec, size_t bytes, double alpha,
-                        int n_steps, unsigned dirs_mask, cudaStream_t s) {
-  if (n_steps == 0) return LQ_OK;
-  const GeomArgs g = geom_args(geom);
+static ApeDirs ape_dirs(unsigned dirs_mask, int* nd_out) {
   ApeDirs ad;
   int nd = 0;
   for (int mu = 0; mu < 4; ++mu)
     if ((dirs_mask >> mu) & 1u) ad.mu[nd++] = mu;
   for (int j = nd; j < 4; ++j) ad.mu[j] = 0;
+  *nd_out = nd;
+  return ad;
+}
+
+lq_status ape_step(const void* in, void* out, const lq_geom& geom, int prec, double alpha, unsigned dirs_mask,
+                   cudaStream_t s) {
+  const GeomArgs g = geom_args(geom);
+  int nd = 0;
+  const ApeDirs ad = ape_dirs(dirs_mask, &nd);
   const double coef = nd > 1 ? alpha / (2.0 * (nd - 1)) : 0.0;   // one direction: no staples
+  const dim3 grid((unsigned)(((g.V + 127) / 128) * nd));
+  if (prec == LQ_F64)
+    k_ape<double><<<grid, 128, 0, s>>>((const double2*)in, (double2*)out, g, 1.0 - alpha, coef, dirs_mask, nd, ad);
+  else
+    k_ape<float><<<grid, 128, 0, s>>>((const float2*)in, (float2*)out, g, (float)(1.0 - alpha), (float)coef,
+                                      dirs_mask, nd, ad);
+  return launch_check("lq_ape_smear kernel");
+}
+
+lq_status ape_run_steps(void* links, void* work, const lq_geom& geom, int prec, size_t bytes, double alpha,
+                        int n_steps, unsigned dirs_mask, cudaStream_t s) {
+  if (n_steps == 0) return LQ_OK;
   const size_t db = bytes / 4;
   lq_status st = LQ_OK;
   for (int mu = 0; mu < 4 && st == LQ_OK; ++mu)   // unsmeared directions pass through both buffers
@@ -66,16 +84,10 @@ lq_status ape_run_steps(void* links, void* work, const lq_geom& geom, int prec, 
       st = cuda_check(cudaMemcpyAsync((char*)work + mu * db, (const char*)links + mu * db, db,
                                       cudaMemcpyDeviceToDevice, s),
                       "lq_ape_smear pass-through copy");
-  const dim3 grid((unsigned)(((g.V + 127) / 128) * nd));
   for (int k = 0; k < n_steps && st == LQ_OK; ++k) {
     const void* in = (k % 2 == 0) ? links : work;
     void* out = (k % 2 == 0) ? work : links;
-    if (prec == LQ_F64)
-      k_ape<double><<<grid, 128, 0, s>>>((const double2*)in, (double2*)out, g, 1.0 - alpha, coef, dirs_mask, nd, ad);
-    else
-      k_ape<float><<<grid, 128, 0, s>>>((const float2*)in, (float2*)out, g, (float)(1.0 - alpha), (float)coef,
-                                        dirs_mask, nd, ad);
-    st = launch_check("lq_ape_smear kernel");
+    st = ape_step(in, out, geom, prec, alpha, dirs_mask, s);
   }
   if (st == LQ_OK && n_steps % 2 == 1)
     for (int mu = 0; mu < 4 && st == LQ_OK; ++mu)

@@ -4,19 +4,28 @@
 //
 // Convention: G_U = dS/dRe U + i dS/dIm U, so dS = Re tr(G^dag dU).  One step
 // U -> U' (per smeared link: C = rho S, Omega = C U^dag, Q, E = exp(iQ),
-// U' = E U) maps G' = G_{U'} to G_U in two kernels:
-//   k_bwd_link:   per smeared link, G_E = G' U^dag,
+// U' = E U) maps G' = G_{U'} to G_U in two stages:
+//   link stage:   per smeared link, G_E = G' U^dag,
 //                 M = tr(G_E^dag B1) Q + tr(G_E^dag B2) Q^2 + f1 G_E^dag + f2 (Q G_E^dag + G_E^dag Q)
 //                 with B_i = sum_j b_ij Q^j, G_Omega = TA(i M^dag);
-//                 writes G_U(local) = E^dag G' + G_Omega^dag C and K = rho G_Omega U
+//                 G_U(local) = E^dag G' + G_Omega^dag C and K = rho G_Omega U
 //                 (the gradient w.r.t. the bare staple sum S).
-//   k_bwd_staple: per link, adds the six staple-insertion terms of K of the
-//                 neighbouring links (the six-term sum of the stout force).
+//   gather stage: per link, G_U = G_U(local) + the six staple-insertion terms
+//                 of K of the neighbouring links (the six-term sum of the stout force).
+// The gather of step j needs K of step j at neighbouring sites, so it cannot
+// share a launch with the link stage of step j; but the link stage of step
+// j-1 needs G at U^(j) only at its own link, which the gather of step j has
+// just formed in registers.  One kernel per step therefore runs the gather of
+// step j followed by the link stage of step j-1 on the same link: the FP32
+// gather's loads and products interleave with the FP64 coefficient work of
+// other warps, and G at U^(j) never goes through HBM.  The first kernel forms
+// the seed (the Wilson-action gradient at U^(n), or a given field) in place of
+// the gather, the last one writes the gradient and the force at the thin links
+// in place of the link stage.
 // The APE force (lq_ape_backward) runs the same recursion with its own link
-// kernel: per smeared link V = (1 - alpha) U + c S, U' = P(V), so
-//   k_ape_bwd_link: G_V from G' through the projection (su3_project.cuh),
-//                   writes G_U(local) = (1 - alpha) G_V and K = c G_V,
-// followed by the same k_bwd_staple.
+// stage: per smeared link V = (1 - alpha) U + c S, U' = P(V), so
+//   G_V from G' through the projection (su3_project.cuh),
+//   G_U(local) = (1 - alpha) G_V and K = c G_V.
 #include <algorithm>
 #include <vector>
 
@@ -37,30 +46,25 @@ template <typename R> __device__ __forceinline__ cx<R> tr_dn(const M3<R>& a, con
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_bwd_link(const V2<R>* __restrict__ U, const V2<R>* __restrict__ Gp,
-                                                  V2<R>* __restrict__ Gout, V2<R>* __restrict__ K, GeomArgs g, R rho,
-                                                  unsigned dirs) {
+__device__ __forceinline__ M3<R> ld(const V2<R>* __restrict__ F, long long V, int dir, int s) {
+  return ld_m3<R>(F + (long long)dir * 9 * V + s, V);
+}
+
+// Link stage of a stout step for the smeared link (s, mu): G' the gradient at
+// U'_mu(x); returns G_U(local) in gl and K in kk.
+template <typename R>
+__device__ __forceinline__ void stout_link_grad(const V2<R>* __restrict__ U, const GeomArgs& g, int s,
+                                                const int c[4], int mu, unsigned dirs, R rho, const M3<R>& Gpm,
+                                                M3<R>& gl, M3<R>& kk) {
   const long long V = g.V;
-  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (sl >= V) return;
-  const int s = (int)sl;
-  const int mu = blockIdx.y;
-  const long long off = (long long)mu * 9 * V + s;
-  if (!((dirs >> mu) & 1u)) {  // not smeared: the gradient passes through
-    st_m3<R>(Gout + off, V, ld_m3<R>(Gp + off, V));
-    return;
-  }
-  int c[4];
-  site_coords(g, s, c);
-  const M3<R> C = m_rscale(staple_sum<R>(U, g, s, c, mu, dirs), rho);
-  const M3<R> Umu = ld_m3<R>(U + off, V);
+  const M3<R> C = m_rscale(staple_sum<R, true>(U, g, s, c, mu, dirs), rho);
+  const M3<R> Umu = ld<R>(U, V, mu, s);
   const QH<R> q = q_from_omega(mul_nd(C, Umu));
   const CHDeriv d = ch_coefficients_deriv<sizeof(R) == 4 ? 1 : 2>(
       to_f64(q.d0), to_f64(q.d1), to_f64(q.d2), mkc(to_f64(q.o01.re), to_f64(q.o01.im)),
       mkc(to_f64(q.o02.re), to_f64(q.o02.im)), mkc(to_f64(q.o12.re), to_f64(q.o12.im)));
   const QH<R> q2 = q_square(q);
   const M3<R> Qf = qh_full(q), Q2f = qh_full(q2);
-  const M3<R> Gpm = ld_m3<R>(Gp + off, V);
   const M3<R> GE = mul_nd(Gpm, Umu);  // G_E = G' U^dag
   // tr(G_E^dag Q^j), j = 0, 1, 2
   const cx<R> t0 = cconj(m_trace(GE));
@@ -87,33 +91,20 @@ __global__ void __launch_bounds__(128) k_bwd_link(const V2<R>* __restrict__ U, c
   const M3<R> GO = m_ta(m_scale(m_adj(M), mkc<R>(0, 1)));
   // E = exp(iQ) and the local gradient E^dag G' + G_Omega^dag C
   const M3<R> E = expiq_assemble(q, q2, mkc<R>(from_f64<R>(d.f[0].re), from_f64<R>(d.f[0].im)), f1, f2);
-  M3<R> Gl = mul_dn(E, Gpm);
-  mac_dn(Gl, GO, C);
-  st_m3<R>(Gout + off, V, Gl);
-  st_m3<R>(K + off, V, m_rscale(mul_nn(GO, Umu), rho));
+  gl = mul_dn(E, Gpm);
+  mac_dn(gl, GO, C);
+  kk = m_rscale(mul_nn(GO, Umu), rho);
 }
 
-// APE step, per smeared link: V recomputed exactly as in the forward kernel
+// Link stage of an APE step: V recomputed exactly as in the forward kernel
 // (staples and mixing in the field precision), the projection's gradient in FP64.
 template <typename R>
-__global__ void __launch_bounds__(128) k_ape_bwd_link(const V2<R>* __restrict__ U, const V2<R>* __restrict__ Gp,
-                                                      V2<R>* __restrict__ Gout, V2<R>* __restrict__ K, GeomArgs g,
-                                                      R keep, R coef, unsigned dirs) {
+__device__ __forceinline__ void ape_link_grad(const V2<R>* __restrict__ U, const GeomArgs& g, int s, const int c[4],
+                                              int mu, unsigned dirs, R keep, R coef, const M3<R>& Gpm, M3<R>& gl,
+                                              M3<R>& kk) {
   const long long V = g.V;
-  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (sl >= V) return;
-  const int s = (int)sl;
-  const int mu = blockIdx.y;
-  const long long off = (long long)mu * 9 * V + s;
-  if (!((dirs >> mu) & 1u)) {  // not smeared: the gradient passes through
-    st_m3<R>(Gout + off, V, ld_m3<R>(Gp + off, V));
-    return;
-  }
-  int c[4];
-  site_coords(g, s, c);
-  const M3<R> C = staple_sum<R>(U, g, s, c, mu, dirs);
-  const M3<R> Umu = ld_m3<R>(U + off, V);
-  const M3<R> Gpm = ld_m3<R>(Gp + off, V);
+  const M3<R> C = staple_sum<R, true>(U, g, s, c, mu, dirs);
+  const M3<R> Umu = ld<R>(U, V, mu, s);
   M3<double> v, gp;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -122,49 +113,36 @@ __global__ void __launch_bounds__(128) k_ape_bwd_link(const V2<R>* __restrict__ 
     gp.e[i] = mkc(to_f64(Gpm.e[i].re), to_f64(Gpm.e[i].im));
   }
   const M3<double> gv = project_su3_vjp_f64<sizeof(R) == 4 ? 1 : 2>(v, gp);
-  M3<R> gl, kk;
   const double kd = (double)keep, cd = (double)coef;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     gl.e[i] = mkc<R>(from_f64<R>(kd * gv.e[i].re), from_f64<R>(kd * gv.e[i].im));
     kk.e[i] = mkc<R>(from_f64<R>(cd * gv.e[i].re), from_f64<R>(cd * gv.e[i].im));
   }
-  st_m3<R>(Gout + off, V, gl);
-  st_m3<R>(K + off, V, kk);
 }
 
+// Gather stage for link (y, a), a in dirs: acc += sum_{mu in dirs, mu != a} [
+//     K_mu(y) U_a(y+mu) U_mu(y+a)^dag + K_mu(y-mu)^dag U_a(y-mu) U_mu(y-mu+a)
+//   + U_mu(y) U_a(y+mu) K_mu(y+a)^dag + U_mu(y-mu)^dag U_a(y-mu) K_mu(y-mu+a)
+//   + U_mu(y-mu)^dag K_a(y-mu) U_mu(y-mu+a) + U_mu(y) K_a(y+mu) U_mu(y+a)^dag ]
+// (10 products per mu: the common factors of the three terms through y+mu
+// and of the three through y-mu are formed once).
 template <typename R>
-__device__ __forceinline__ M3<R> ld(const V2<R>* __restrict__ F, long long V, int dir, int s) {
-  return ld_m3<R>(F + (long long)dir * 9 * V + s, V);
-}
-
-// G_alpha(y) += sum_{mu in dirs, mu != alpha} [ K_mu(y) U_a(y+mu) U_mu(y+a)^dag
-//                 + K_mu(y-mu)^dag U_a(y-mu) U_mu(y-mu+a) + U_mu(y) U_a(y+mu) K_mu(y+a)^dag
-//                 + U_mu(y-mu)^dag U_a(y-mu) K_mu(y-mu+a)
-//                 + U_mu(y-mu)^dag K_a(y-mu) U_mu(y-mu+a) + U_mu(y) K_a(y+mu) U_mu(y+a)^dag ]
-// The four directions of a block of sites run in consecutive CTAs, so the
-// neighbour links and K they share are read while still in L2.
-template <typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_bwd_staple(const V2<R>* __restrict__ U, const V2<R>* __restrict__ K,
-                                                    V2<R>* __restrict__ G, GeomArgs g, unsigned dirs) {
+__device__ __forceinline__ void staple_gather(const V2<R>* __restrict__ U, const V2<R>* __restrict__ K,
+                                              const GeomArgs& g, int s, const int c[4], int a, unsigned dirs,
+                                              M3<R>& acc) {
   const long long V = g.V;
-  const long long sl = (long long)(blockIdx.x / 4) * blockDim.x + threadIdx.x;
-  if (sl >= V) return;
-  const int s = (int)sl;
-  const int a = blockIdx.x % 4;
-  if (!((dirs >> a) & 1u)) return;
-  int c[4];
-  site_coords(g, s, c);
-  const int s_pa = nb_fwd(g, s, coord_of(c, a), a);
-  M3<R> acc = ld<R>(G, V, a, s);
-#pragma unroll
+  const int s_pa = nb_fwd_rt(g, s, coord_of(c, a), a);
+  // not unrolled: one copy of the ten products keeps the kernel's code small
+#pragma unroll 1
   for (int mu = 0; mu < 4; ++mu) {
     if (mu == a || !((dirs >> mu) & 1u)) continue;
-    const int s_pmu = nb_fwd(g, s, c[mu], mu);
-    const int s_mmu = nb_bwd(g, s, c[mu], mu);
-    const int s_mmu_pa = nb_bwd(g, s_pa, c[mu], mu);  // y - mu + a
+    const int cm = coord_of(c, mu);
+    const int s_pmu = nb_fwd_rt(g, s, cm, mu);
+    const int s_mmu = nb_bwd_rt(g, s, cm, mu);
+    const int s_mmu_pa = nb_bwd_rt(g, s_pa, cm, mu);  // y - mu + a
     // the three terms through y+mu, with A = U_mu(y), B = U_a(y+mu):
-    //   (K_mu(y) B + A K_a(y+mu)) U_mu(y+a)^dag + (A B) K_mu(y+a)^dag   (5 products, not 6)
+    //   (K_mu(y) B + A K_a(y+mu)) U_mu(y+a)^dag + (A B) K_mu(y+a)^dag
     {
       const M3<R> A = ld<R>(U, V, mu, s), B = ld<R>(U, V, a, s_pmu);
       M3<R> T = mul_nn(ld<R>(K, V, mu, s), B);
@@ -182,7 +160,76 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_bwd_staple(cons
       mac_nn(acc, mul_dn(A, B), ld<R>(K, V, mu, s_mmu_pa));
     }
   }
-  st_m3<R>(G + (long long)a * 9 * V + s, V, acc);
+}
+
+// Where the gradient G' at U^(j+1) comes from, and what is done with it.
+enum BwdSrc { kSrcLoad = 0, kSrcWilson = 1, kSrcGather = 2 };
+enum BwdDst { kDstStout = 0, kDstApe = 1, kDstFinal = 2 };
+
+template <typename R> struct BwdArgs {
+  const V2<R>* Unext;  // U^(j+1): links of the Wilson seed or of the gather
+  const V2<R>* Knext;  // K of step j+1 (gather)
+  const V2<R>* Gin;    // the seed (load), or G_U(local) of step j+1 (gather)
+  const V2<R>* Ucur;   // U^(j), input of step j (link stage); the thin links (final)
+  V2<R>* Gout;         // G_U(local) of step j (link stage); G at the thin links (final, may be NULL)
+  V2<R>* Kout;         // K of step j (link stage)
+  V2<R>* Fout;         // force TA(G U^dag) at the thin links (final, may be NULL)
+  GeomArgs g;
+  R w0, w1;            // stout: rho; APE: 1 - alpha and the staple coefficient
+  R mbeta3;            // Wilson seed: -beta / 3
+  unsigned dirs;
+};
+
+// One thread per link; the four directions of a block of 128 sites run in
+// consecutive CTAs, so the neighbour links and K that the gathers and staple
+// sums of a site block share are read while still in L1/L2.
+template <typename R, int SRC, int DST>
+__global__ void __launch_bounds__(128) k_bwd_step(BwdArgs<R> p) {
+  const GeomArgs& g = p.g;
+  const long long V = g.V;
+  const long long sl = (long long)(blockIdx.x / 4) * blockDim.x + threadIdx.x;
+  if (sl >= V) return;
+  const int s = (int)sl;
+  const int a = blockIdx.x % 4;
+  const long long off = (long long)a * 9 * V + s;
+  int c[4];
+  site_coords(g, s, c);
+  // G' = G at U^(j+1) for the link (s, a)
+  M3<R> Gp;
+  if (SRC == kSrcWilson) {
+    Gp = m_rscale(staple_sum<R, true>(p.Unext, g, s, c, a, 15u), p.mbeta3);
+  } else {
+    Gp = ld_m3<R>(p.Gin + off, V);
+    if (SRC == kSrcGather && ((p.dirs >> a) & 1u)) staple_gather<R>(p.Unext, p.Knext, g, s, c, a, p.dirs, Gp);
+  }
+  if (DST == kDstFinal) {
+    if (p.Gout) st_m3<R>(p.Gout + off, V, Gp);
+    if (p.Fout) st_m3<R>(p.Fout + off, V, m_ta(mul_nd(Gp, ld_m3<R>(p.Ucur + off, V))));
+    return;
+  }
+  if (!((p.dirs >> a) & 1u)) {  // not smeared: the gradient passes through
+    st_m3<R>(p.Gout + off, V, Gp);
+    return;
+  }
+  M3<R> gl, kk;
+  if (DST == kDstStout) stout_link_grad<R>(p.Ucur, g, s, c, a, p.dirs, p.w0, Gp, gl, kk);
+  else ape_link_grad<R>(p.Ucur, g, s, c, a, p.dirs, p.w0, p.w1, Gp, gl, kk);
+  st_m3<R>(p.Gout + off, V, gl);
+  st_m3<R>(p.Kout + off, V, kk);
+}
+
+template <typename R, int SRC, int DST>
+static lq_status launch_bwd_step(const BwdArgs<R>& p, cudaStream_t s) {
+  const unsigned grid = (unsigned)(((p.g.V + 127) / 128) * 4);
+  k_bwd_step<R, SRC, DST><<<grid, 128, 0, s>>>(p);
+  return launch_check("k_bwd_step");
+}
+
+template <typename R, int DST>
+static lq_status launch_bwd_src(int src, const BwdArgs<R>& p, cudaStream_t s) {
+  if (src == kSrcLoad) return launch_bwd_step<R, kSrcLoad, DST>(p, s);
+  if (src == kSrcWilson) return launch_bwd_step<R, kSrcWilson, DST>(p, s);
+  return launch_bwd_step<R, kSrcGather, DST>(p, s);
 }
 
 // Wilson-action gradient G_mu(x) = -(beta/3) * (sum over all nu != mu of the staples).
@@ -236,99 +283,163 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
   const GeomArgs g = geom_args(thin->geom);
   const long long V = g.V;
   const size_t fb = thin->bytes;
+  const size_t db = fb / 4;   // one direction's planes
   Bufs b;
   b.s = s;
-  auto alloc = [&](void** p) -> lq_status {
-    lq_status st = scratch_alloc(p, fb, s, who);
-    if (st == LQ_OK) b.own.push_back(*p);
-    return st;
-  };
   lq_status st;
-  // checkpoints: ck[j] holds U^(j) for j % every == 0 (ck[0] is the thin field itself)
-  std::vector<void*> ck(n + 1, nullptr);
-  ck[0] = thin->ptr;
-  void *w0, *w1, *Ga, *Gb, *Kb = nullptr;   // Kb: staple-sum gradient (stout and APE only)
-  if ((st = alloc(&w0)) || (st = alloc(&w1)) || (st = alloc(&Ga)) || (st = alloc(&Gb))) return st;
-  if (kind != Smearing::kHyp && (st = alloc(&Kb))) return st;
-  for (int j = every; j < n; j += every)
-    if ((st = alloc(&ck[j]))) return st;
+  // a scratch link field whose unsmeared directions hold the thin links'
+  // (step kernels never write those, so they stay valid in every buffer)
+  auto alloc_links = [&](void** p) -> lq_status {
+    lq_status st2 = scratch_alloc(p, fb, s, who);
+    if (st2 != LQ_OK) return st2;
+    b.own.push_back(*p);
+    for (int mu = 0; mu < 4 && st2 == LQ_OK; ++mu)
+      if (!((dirs >> mu) & 1u))
+        st2 = cuda_check(cudaMemcpyAsync((char*)*p + mu * db, (const char*)thin->ptr + mu * db, db,
+                                         cudaMemcpyDeviceToDevice, s),
+                         who);
+    return st2;
+  };
+  auto alloc = [&](void** p) -> lq_status {
+    lq_status st2 = scratch_alloc(p, fb, s, who);
+    if (st2 == LQ_OK) b.own.push_back(*p);
+    return st2;
+  };
   void* hyp_scratch = nullptr;   // decorated links and their gradients
   if (kind == Smearing::kHyp && n > 0) {
     if ((st = scratch_alloc(&hyp_scratch, kHypBwdPlanes * (fb / 4), s, who))) return st;
     b.own.push_back(hyp_scratch);
   }
-  TuneChoice tc = stout_default_choice(thin->prec);
-  // recomputed fields follow lq_stout_smear's default (FP32 links are re-projected)
+  // recomputed fields follow the forward entry points' defaults (FP32 stout
+  // links are re-projected)
+  const TuneChoice tc = stout_default_choice(thin->prec);
   const int reproject = thin->prec == LQ_F32 ? 1 : 0;
-  auto run_steps = [&](void* links, int steps) -> lq_status {
-    if (kind == Smearing::kApe) return ape_run_steps(links, w1, thin->geom, thin->prec, fb, w, steps, dirs, s);
-    if (kind == Smearing::kHyp)
-      return hyp_run_steps(links, w1, hyp_scratch, thin->geom, thin->prec, fb, sa.a[0], sa.a[1], sa.a[2], steps, s);
-    return stout_run_steps(links, w1, thin->geom, thin->prec, w, steps, dirs, reproject, tc, s);
-  };
-  int nd = 0;
-  for (int mu = 0; mu < 4; ++mu) nd += (dirs >> mu) & 1u;
-  const double ape_coef = nd > 1 ? w / (2.0 * (nd - 1)) : 0.0;   // as in lq_ape_smear
-  // forward: U^(j) from the nearest stored checkpoint at or below j (stored
-  // indices are multiples of `every` below n), into dst
-  auto forward_to = [&](int j, void* dst) -> lq_status {
-    int j0 = (j / every) * every;
-    if (j0 >= n) j0 = ((n - 1) / every) * every;
-    lq_status st2 = cuda_check(cudaMemcpyAsync(dst, ck[j0], fb, cudaMemcpyDeviceToDevice, s), who);
+  void* hyp_work = nullptr;
+  // one step from `in` into `out` (distinct fields)
+  auto step = [&](const void* in, void* out) -> lq_status {
+    if (kind == Smearing::kStout)
+      return stout_step_range(in, out, thin->geom, thin->prec, w, dirs, reproject, tc, 0, V, s);
+    if (kind == Smearing::kApe) return ape_step(in, out, thin->geom, thin->prec, w, dirs, s);
+    lq_status st2 = cuda_check(cudaMemcpyAsync(out, in, fb, cudaMemcpyDeviceToDevice, s), who);
     if (st2 != LQ_OK) return st2;
-    return run_steps(dst, j - j0);
+    return hyp_run_steps(out, hyp_work, hyp_scratch, thin->geom, thin->prec, fb, sa.a[0], sa.a[1], sa.a[2], 1, s);
   };
-  for (int j = every; j < n; j += every) {  // ck[j] = `every` steps from ck[j - every]
-    if ((st = cuda_check(cudaMemcpyAsync(ck[j], ck[j - every], fb, cudaMemcpyDeviceToDevice, s), who)))
-      return st;
-    if ((st = run_steps(ck[j], every))) return st;
+  if (kind == Smearing::kHyp && n > 0 && (st = alloc(&hyp_work))) return st;
+  // checkpoints: ck[j] holds U^(j) for j % every == 0, j < n (ck[0] is the thin field itself)
+  std::vector<const void*> ck(n + 1, nullptr);
+  ck[0] = thin->ptr;
+  for (int j = every; j < n; j += every) {
+    void* p = nullptr;
+    if ((st = alloc_links(&p))) return st;
+    ck[j] = p;
   }
-  // seed at U^(n)
-  if (seed) {
-    if ((st = cuda_check(cudaMemcpyAsync(Ga, seed->ptr, fb, cudaMemcpyDeviceToDevice, s), who)))
-      return st;
-  } else {
-    void* Un = thin->ptr;
-    if (n > 0) {
-      if ((st = forward_to(n, w0))) return st;
-      Un = w0;
+  // two fields for recomputed U^(j) (the one in use and the next), one for
+  // the ping-pong of the recomputation
+  void* rbuf[2] = {nullptr, nullptr};
+  void* rtmp = nullptr;
+  const bool need_u_n = !seed && n > 0;
+  const bool recompute = every > 1 && n > 1;
+  if ((need_u_n || recompute) && (st = alloc_links(&rbuf[0]))) return st;
+  if (recompute && ((st = alloc_links(&rbuf[1])) || (st = alloc_links(&rtmp)))) return st;
+  // U^(j0 + m) from src = U^(j0) into dst (m >= 1), through rtmp when m >= 2
+  auto advance = [&](const void* src, void* dst, int m) -> lq_status {
+    const void* in = src;
+    for (int k = 0; k < m; ++k) {
+      void* out = ((m - 1 - k) % 2 == 0) ? dst : rtmp;
+      lq_status st2 = step(in, out);
+      if (st2 != LQ_OK) return st2;
+      in = out;
     }
-    dim3 grid((unsigned)((V + 127) / 128), 4);
-    k_wilson_grad<R><<<grid, 128, 0, s>>>((const V2<R>*)Un, (V2<R>*)Ga, g, (R)(-beta / 3.0));
-    if ((st = launch_check("k_wilson_grad"))) return st;
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    const void* Uj = ck[j];
-    if (!Uj) {
-      if ((st = forward_to(j, w0))) return st;
-      Uj = w0;
+    return LQ_OK;
+  };
+  for (int j = every; j < n; j += every)
+    if ((st = advance(ck[j - every], (void*)ck[j], every))) return st;
+  // U^(j) from the nearest checkpoint below it, into a buffer other than `keep`
+  auto get_links = [&](int j, const void* keep) -> const void* {
+    if (ck[j]) return ck[j];
+    const int j0 = (j / every) * every;
+    void* dst = rbuf[0] != keep ? rbuf[0] : rbuf[1];
+    return advance(ck[j0], dst, j - j0) == LQ_OK ? dst : nullptr;
+  };
+  if (kind == Smearing::kHyp) {
+    // the HYP force keeps its per-level kernels (hyp.cu): seed, steps, force
+    void *Ga, *Gb;
+    if ((st = alloc(&Ga)) || (st = alloc(&Gb))) return st;
+    if (seed) {
+      if ((st = cuda_check(cudaMemcpyAsync(Ga, seed->ptr, fb, cudaMemcpyDeviceToDevice, s), who))) return st;
+    } else {
+      const void* Un = thin->ptr;
+      if (n > 0) {
+        const int j0 = ((n - 1) / every) * every;
+        if ((st = advance(ck[j0], rbuf[0], n - j0))) return st;
+        Un = rbuf[0];
+      }
+      dim3 grid((unsigned)((V + 127) / 128), 4);
+      k_wilson_grad<R><<<grid, 128, 0, s>>>((const V2<R>*)Un, (V2<R>*)Ga, g, (R)(-beta / 3.0));
+      if ((st = launch_check("k_wilson_grad"))) return st;
     }
-    if (kind == Smearing::kHyp) {
+    for (int j = n - 1; j >= 0; --j) {
+      const void* Uj = get_links(j, nullptr);
+      if (!Uj) return LQ_ERR_CUDA;
       if ((st = hyp_backward_step(Uj, Ga, Gb, hyp_scratch, thin->geom, thin->prec, fb, sa.a[0], sa.a[1], sa.a[2], s)))
         return st;
       std::swap(Ga, Gb);
-      continue;
     }
-    dim3 grid((unsigned)((V + 127) / 128), 4);
-    if (kind == Smearing::kApe)
-      k_ape_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g,
-                                             (R)(1.0 - w), (R)ape_coef, dirs);
-    else
-      k_bwd_link<R><<<grid, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Ga, (V2<R>*)Gb, (V2<R>*)Kb, g, (R)w, dirs);
-    if ((st = launch_check("backward link kernel"))) return st;
-    k_bwd_staple<R><<<grid.x * 4, 128, 0, s>>>((const V2<R>*)Uj, (const V2<R>*)Kb, (V2<R>*)Gb, g, dirs);
-    if ((st = launch_check("k_bwd_staple"))) return st;
+    if (force) {
+      dim3 grid((unsigned)((V + 255) / 256), 4);
+      k_force<R><<<grid, 256, 0, s>>>((const V2<R>*)thin->ptr, (const V2<R>*)Ga, (V2<R>*)force->ptr, V);
+      if ((st = launch_check("k_force"))) return st;
+    }
+    if (grad_out)
+      if ((st = cuda_check(cudaMemcpyAsync(grad_out->ptr, Ga, fb, cudaMemcpyDeviceToDevice, s), who))) return st;
+    return LQ_OK;
+  }
+  // stout and APE: one fused kernel per step (gather of step j + link stage of step j-1)
+  int nd = 0;
+  for (int mu = 0; mu < 4; ++mu) nd += (dirs >> mu) & 1u;
+  BwdArgs<R> p{};
+  p.g = g;
+  p.dirs = dirs;
+  p.mbeta3 = (R)(-beta / 3.0);
+  if (kind == Smearing::kStout) {
+    p.w0 = (R)w;
+  } else {
+    p.w0 = (R)(1.0 - w);
+    p.w1 = (R)(nd > 1 ? w / (2.0 * (nd - 1)) : 0.0);   // as in lq_ape_smear
+  }
+  const int dst_link = kind == Smearing::kStout ? kDstStout : kDstApe;
+  int src = seed ? kSrcLoad : kSrcWilson;
+  p.Gin = seed ? (const V2<R>*)seed->ptr : nullptr;
+  if (need_u_n) {   // U^(n) for the Wilson seed
+    const int j0 = ((n - 1) / every) * every;
+    if ((st = advance(ck[j0], rbuf[0], n - j0))) return st;
+    p.Unext = (const V2<R>*)rbuf[0];
+  } else if (!seed) {
+    p.Unext = (const V2<R>*)thin->ptr;   // n = 0: the seed at the thin links
+  }
+  void *Ga = nullptr, *Gb = nullptr, *Ka = nullptr, *Kb = nullptr;
+  if (n > 0 && ((st = alloc(&Ga)) || (st = alloc(&Gb)) || (st = alloc(&Ka)) || (st = alloc(&Kb)))) return st;
+  for (int j = n - 1; j >= 0; --j) {
+    const void* Uj = get_links(j, p.Unext);
+    if (!Uj) return LQ_ERR_CUDA;
+    p.Ucur = (const V2<R>*)Uj;
+    p.Gout = (V2<R>*)Ga;
+    p.Kout = (V2<R>*)Ka;
+    st = dst_link == kDstStout ? launch_bwd_src<R, kDstStout>(src, p, s) : launch_bwd_src<R, kDstApe>(src, p, s);
+    if (st != LQ_OK) return st;
+    // the next kernel gathers step j's K on U^(j)
+    src = kSrcGather;
+    p.Unext = (const V2<R>*)Uj;
+    p.Knext = (const V2<R>*)Ka;
+    p.Gin = (const V2<R>*)Ga;
     std::swap(Ga, Gb);
+    std::swap(Ka, Kb);
   }
-  if (force) {
-    dim3 grid((unsigned)((V + 255) / 256), 4);
-    k_force<R><<<grid, 256, 0, s>>>((const V2<R>*)thin->ptr, (const V2<R>*)Ga, (V2<R>*)force->ptr, V);
-    if ((st = launch_check("k_force"))) return st;
-  }
-  if (grad_out)
-    if ((st = cuda_check(cudaMemcpyAsync(grad_out->ptr, Ga, fb, cudaMemcpyDeviceToDevice, s), who)))
-      return st;
-  return LQ_OK;
+  p.Ucur = (const V2<R>*)thin->ptr;
+  p.Gout = grad_out ? (V2<R>*)grad_out->ptr : nullptr;
+  p.Kout = nullptr;
+  p.Fout = force ? (V2<R>*)force->ptr : nullptr;
+  return launch_bwd_src<R, kDstFinal>(src, p, s);
 }
 
 }  // namespace lq

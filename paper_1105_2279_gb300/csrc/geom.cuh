@@ -32,5 +32,17 @@ __device__ __forceinline__ int nb_fwd(const GeomArgs& g, int s, int c_nu, int nu
 __device__ __forceinline__ int nb_bwd(const GeomArgs& g, int s, int c_nu, int nu) {
   return (c_nu > 0) ? s - g.stride[nu] : s + (g.L[nu] - 1) * g.stride[nu];
 }
+// The same for a direction known only at run time: extent and stride picked
+// by selects, so the geometry is never indexed (and copied to local memory).
+__device__ __forceinline__ int nb_fwd_rt(const GeomArgs& g, int s, int c_nu, int nu) {
+  const int L = nu == 0 ? g.L[0] : (nu == 1 ? g.L[1] : (nu == 2 ? g.L[2] : g.L[3]));
+  const int st = nu == 0 ? g.stride[0] : (nu == 1 ? g.stride[1] : (nu == 2 ? g.stride[2] : g.stride[3]));
+  return (c_nu + 1 < L) ? s + st : s - (L - 1) * st;
+}
+__device__ __forceinline__ int nb_bwd_rt(const GeomArgs& g, int s, int c_nu, int nu) {
+  const int L = nu == 0 ? g.L[0] : (nu == 1 ? g.L[1] : (nu == 2 ? g.L[2] : g.L[3]));
+  const int st = nu == 0 ? g.stride[0] : (nu == 1 ? g.stride[1] : (nu == 2 ? g.stride[2] : g.stride[3]));
+  return (c_nu > 0) ? s - st : s + (L - 1) * st;
+}
 
 }  // namespace lq

@@ -104,6 +104,10 @@ TuneChoice stout_default_choice(int prec);
 // scratch field of the same size; the arithmetic of lq_ape_smear.
 lq_status ape_run_steps(void* links, void* work, const lq_geom& g, int prec, size_t bytes, double alpha,
                         int n_steps, unsigned dirs, cudaStream_t s);
+// One APE step from `in` to `out` (distinct fields); directions outside dirs
+// are not written.
+lq_status ape_step(const void* in, void* out, const lq_geom& g, int prec, double alpha, unsigned dirs,
+                   cudaStream_t s);
 // n HYP steps in place; scratch holds 24 colour-matrix planes (bytes / 4 each).
 lq_status hyp_run_steps(void* links, void* work, void* scratch, const lq_geom& g, int prec, size_t bytes,
                         double a1, double a2, double a3, int n_steps, cudaStream_t s);

@@ -18,14 +18,17 @@ __device__ __forceinline__ M3<R> ld_link(const typename vec2<R>::type* __restric
 
 // sum over nu in dirs, nu != mu, of
 //   U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
-template <typename R>
+// SEL: the neighbour x+mu by selects on the geometry instead of indexing it
+// (kernels whose geometry sits in a parameter struct would copy it to local
+// memory to index it).
+template <typename R, bool SEL = false>
 __device__ __forceinline__ M3<R> staple_sum(const typename vec2<R>::type* __restrict__ U,
                                             const GeomArgs& g, int s, const int c[4], int mu,
                                             unsigned dirs) {
   const long long V = g.V;
   M3<R> C;
   m_zero(C);
-  const int s_pmu = nb_fwd(g, s, coord_of(c, mu), mu);
+  const int s_pmu = SEL ? nb_fwd_rt(g, s, coord_of(c, mu), mu) : nb_fwd(g, s, coord_of(c, mu), mu);
   // not unrolled: one copy of the six products keeps the kernel's hot code
   // small (instruction-fetch stalls dominated the unrolled form)
 #pragma unroll 1
@@ -222,29 +225,33 @@ __device__ __forceinline__ void expiq_series(double c0, double c1, int K, CHCoef
 //   x' = c0 z + a_n,  dx'/dc0 = c0 dz/dc0 + z,  dx'/dc1 = c0 dz/dc1
 //   y' = x + c1 z,    dy'/dc0 = dx/dc0 + c1 dz/dc0,  dy'/dc1 = dx/dc1 + c1 dz/dc1 + z
 //   z' = y.
+// The c1 derivative is carried as X1 = dx/dc1 + z, which obeys
+//   X1' = c0 dz/dc1 + y,  dy'/dc1 = c1 dz/dc1 + X1,
+// two FMAs per component instead of a product, an FMA and an addition;
+// dx/dc1 = X1 - z at the end.
 // Without the series' cancellation-free form the closed-form b_ij lose
 // accuracy like 1e-16 / |Q|^4 as Q -> 0.  One more pair of terms than the
 // f_j alone keeps b_ij Q^j at FP64 rounding for all c1 <= 3/4.
 template <int KMAX>
 __device__ __forceinline__ void expiq_series_deriv(double c0, double c1, int K, cx<double> f[3],
                                                    cx<double> b1[3], cx<double> b2[3]) {
-  cx<double> x = mkc(0.0, 0.0), y = x, z = x, x0 = x, y0 = x, z0 = x, x1 = x, y1 = x, z1 = x;
+  cx<double> x = mkc(0.0, 0.0), y = x, z = x, x0 = x, y0 = x, z0 = x, X1 = x, y1 = x, z1 = x;
 #pragma unroll
   for (int n = 2 * KMAX + 1; n >= 0; --n) {
     if (n <= 2 * K + 1) {
       const cx<double> a = (n & 1) ? mkc(0.0, kExpSeriesA[n]) : mkc(kExpSeriesA[n], 0.0);
       const cx<double> nx = mkc(fma(z.re, c0, a.re), fma(z.im, c0, a.im));
       const cx<double> nx0 = mkc(fma(z0.re, c0, z.re), fma(z0.im, c0, z.im));
-      const cx<double> nx1 = mkc(z1.re * c0, z1.im * c0);
+      const cx<double> nX1 = mkc(fma(z1.re, c0, y.re), fma(z1.im, c0, y.im));
       const cx<double> ny = mkc(fma(z.re, c1, x.re), fma(z.im, c1, x.im));
       const cx<double> ny0 = mkc(fma(z0.re, c1, x0.re), fma(z0.im, c1, x0.im));
-      const cx<double> ny1 = mkc(fma(z1.re, c1, x1.re + z.re), fma(z1.im, c1, x1.im + z.im));
+      const cx<double> ny1 = mkc(fma(z1.re, c1, X1.re), fma(z1.im, c1, X1.im));
       z = y;
       z0 = y0;
       z1 = y1;
       x = nx;
       x0 = nx0;
-      x1 = nx1;
+      X1 = nX1;
       y = ny;
       y0 = ny0;
       y1 = ny1;
@@ -253,7 +260,7 @@ __device__ __forceinline__ void expiq_series_deriv(double c0, double c1, int K, 
   f[0] = x;
   f[1] = y;
   f[2] = z;
-  b1[0] = x1;
+  b1[0] = mkc(X1.re - z.re, X1.im - z.im);
   b1[1] = y1;
   b1[2] = z1;
   b2[0] = x0;

@@ -172,3 +172,26 @@ def test_force_vanishes_on_unit_field(gpu, prec):
     U = fieldgen.unit_links((3, 4, 2, 3))
     F, G = gpu_force(U, prec, 0.1, 2, ALL)
     assert np.max(np.abs(F)) <= (1e-14 if prec == lq.LQ_F64 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+@pytest.mark.parametrize("with_seed", [False, True])
+def test_checkpoint_policies_and_outputs_agree(gpu, prec, with_seed):
+    """Every checkpoint policy recomputes the same U^(j) with the same kernels,
+    so the force is bit-identical across them; the force alone and the
+    gradient alone equal the outputs of a call that asks for both."""
+    dims = (4, 3, 4, 3)
+    U = fieldgen.near_identity_su3(dims, 303)
+    seed = fieldgen.haar_su3(dims, 304) * 0.5 if with_seed else None
+    F1, G1 = gpu_force(U, prec, 0.1, 4, ALL, seed=seed, every=1)
+    for every in (2, 3, 5):
+        F, G = gpu_force(U, prec, 0.1, 4, ALL, seed=seed, every=every)
+        assert np.array_equal(F, F1) and np.array_equal(G, G1), every
+    f = upload_links(U, prec)
+    s = upload_links(seed, prec) if seed is not None else None
+    F_only = lq.Field(f.geom, lq.LQ_LINKS, prec)
+    lq.stout_backward(f, 0.1, 4, ALL, F_only, grad_seed=s, beta=6.0)
+    G_only = lq.Field(f.geom, lq.LQ_LINKS, prec)
+    lq.stout_backward(f, 0.1, 4, ALL, None, grad_seed=s, beta=6.0, grad_out=G_only)
+    assert np.array_equal(F_only.download(), F1)
+    assert np.array_equal(G_only.download(), G1)

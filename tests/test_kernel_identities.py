@@ -95,3 +95,46 @@ def test_reprojection_split_is_gram_schmidt():
         assert np.max(np.abs(s0 - r0)) < 1e-15
         assert np.max(np.abs(s1 - r1)) < 1e-15
         assert np.max(np.abs(s2 - r2)) < 1e-15
+
+
+def _series_deriv(c0, c1, K):
+    """numpy restatement of the kernels' differentiated Horner series of
+    exp(iQ) reduced by Q^3 = c1 Q + c0 (degree 2K+1), with the c1 derivative
+    carried as X1 = dx/dc1 + z: returns f_j, df_j/dc1, df_j/dc0."""
+    from math import factorial
+    x = y = z = x0 = y0 = z0 = X1 = y1 = z1 = 0j
+    for n in range(2 * K + 1, -1, -1):
+        a = (1j ** n) / factorial(n)
+        x, x0, X1, y, y0, y1, z, z0, z1 = (c0 * z + a, c0 * z0 + z, c0 * z1 + y, c1 * z + x, c1 * z0 + x0,
+                                           c1 * z1 + X1, y, y0, y1)
+    return np.array([x, y, z]), np.array([X1 - z, y1, z1]), np.array([x0, y0, z0])
+
+
+def _diag_q(c0, c1):
+    """Diagonal traceless Hermitian Q with det Q = c0 and tr(Q^2)/2 = c1 (the
+    roots of l^3 - c1 l - c0)."""
+    lam = np.sort(np.real(np.roots([1.0, 0.0, -c1, -c0])))
+    return np.diag(lam).astype(np.complex128)
+
+
+@pytest.mark.parametrize("c1,frac", [(0.02, 0.3), (0.3, -0.7), (0.74, 0.95), (0.01, -0.1)])
+def test_series_derivative_recurrence(c1, frac):
+    """f_j of the series equal the oracle's Cayley-Hamilton coefficients, and
+    its c1 and c0 derivatives equal central differences of the oracle's f_j
+    (spectra with the prescribed c0, c1 from the characteristic cubic)."""
+    from oracle import stout
+    c0 = frac * 2.0 * (c1 / 3.0) ** 1.5
+    f, b1, b2 = _series_deriv(c0, c1, 10)
+    ref = np.array(stout.ch_coefficients(_diag_q(c0, c1)))
+    # f_j multiplies Q^j ~ c1^(j/2) (the closed form loses eps/c1^(j/2) on f_j as Q -> 0)
+    scale = np.sqrt(c1) ** np.arange(3)
+    assert np.max(np.abs(f - ref) * scale) <= 1e-14
+    h1 = 1e-5 * c1
+    d1 = (np.array(stout.ch_coefficients(_diag_q(c0, c1 + h1))) -
+          np.array(stout.ch_coefficients(_diag_q(c0, c1 - h1)))) / (2 * h1)
+    c0max = 2.0 * (c1 / 3.0) ** 1.5
+    h0 = 1e-5 * c0max
+    d0 = (np.array(stout.ch_coefficients(_diag_q(c0 + h0, c1))) -
+          np.array(stout.ch_coefficients(_diag_q(c0 - h0, c1)))) / (2 * h0)
+    assert np.max(np.abs(b1 - d1)) <= 1e-6 * max(1.0, np.max(np.abs(d1)))
+    assert np.max(np.abs(b2 - d0)) <= 1e-6 * max(1.0, np.max(np.abs(d0)))
