@@ -214,7 +214,12 @@ typedef struct lq_stout_opts {
   int struct_size;        /* sizeof(lq_stout_opts); 0 => all defaults               */
   int reproject;          /* -1 default (on for LQ_F32 links, off for LQ_F64), 0, 1 */
   int use_graph;          /* 1: record the n-step launch sequence as a CUDA graph
-                             and replay it (cached per field, dims, n, rho, dirs)   */
+                             and replay it.  The recorded graph and its links-sized
+                             workspace are kept per (field pointer, dims, n, rho,
+                             dirs, launch shape, device) until lq_free_all; at most
+                             8 are kept (least recently launched dropped first).
+                             Calls with the same key share that workspace, so two
+                             such calls must not overlap on the GPU.                */
   int variant;            /* 0 tuned/default, 1 global-load kernel,
                              2 shared-memory staged kernel (FP32 links),
                              3 two kernels per step: the two-link products
@@ -305,7 +310,16 @@ lq_status lq_stout_backward(const lq_field* thin_links, double rho, int n_steps,
 /* Smears n_cfg independent LINKS fields (any geometries, one precision) with
  * one persistent launch per step over a device work list of (config, tile)
  * items; with opts->use_graph the n-step sequence is a replayed CUDA graph.
- * Results equal n_cfg separate lq_stout_smear calls bit for bit. */
+ * Results equal n_cfg separate lq_stout_smear calls bit for bit.
+ * Memory: the work list (n_cfg descriptors) is kept per (field pointers,
+ * dims, launch shape, dirs, device), at most 16 lists, least recently used
+ * dropped first.  Without use_graph the double buffer (the size of all the
+ * fields together) and the step counters come stream-ordered from the
+ * library pool on every call and go back to it at the end of the call.  With
+ * use_graph the recorded graph owns its double buffer and counters, kept per
+ * (work-list key, n_steps, rho, reproject) until lq_free_all, at most 4
+ * graphs; calls with the same graph key share them, so two such calls must
+ * not overlap on the GPU. */
 lq_status lq_stout_smear_batch(lq_field* const* links, int n_cfg, double rho, int n_steps,
                                unsigned dirs_mask, const lq_stout_opts* opts, void* stream);
 

@@ -604,19 +604,26 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   void* work = nullptr;
   void* wfield = nullptr;   // two-link products (variant 3)
+  unsigned long long used = 0;
 };
+// At most kMaxGraphs recorded sequences are kept (each holds a links-sized
+// workspace); the least recently launched one is dropped first.
+constexpr size_t kMaxGraphs = 8;
 static std::mutex g_graph_mu;
+static unsigned long long g_graph_tick = 0;
 static std::map<GraphKey, GraphEntry>& graph_cache() {
   static std::map<GraphKey, GraphEntry> m;
   return m;
 }
+static void free_graph_entry(GraphEntry& e) {
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (e.work) cudaFree(e.work);
+  if (e.wfield) cudaFree(e.wfield);
+  e = GraphEntry();
+}
 static void release_graphs() {
   std::lock_guard<std::mutex> lk(g_graph_mu);
-  for (auto& kv : graph_cache()) {
-    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
-    if (kv.second.work) cudaFree(kv.second.work);
-    if (kv.second.wfield) cudaFree(kv.second.wfield);
-  }
+  for (auto& kv : graph_cache()) free_graph_entry(kv.second);
   graph_cache().clear();
 }
 
@@ -637,8 +644,16 @@ static lq_status run_graph(lq_field* f, double rho, int n, unsigned dirs, int re
   k.dirs = dirs;
   k.rho = rho;
   std::lock_guard<std::mutex> lk(g_graph_mu);
+  const unsigned long long now = ++g_graph_tick;
   auto it = graph_cache().find(k);
   if (it == graph_cache().end()) {
+    while (graph_cache().size() >= kMaxGraphs) {   // cudaFree waits for launches still using the entry
+      auto old = graph_cache().begin();
+      for (auto j = graph_cache().begin(); j != graph_cache().end(); ++j)
+        if (j->second.used < old->second.used) old = j;
+      free_graph_entry(old->second);
+      graph_cache().erase(old);
+    }
     GraphEntry e;
     lq_status st = cuda_check(cudaMalloc(&e.work, f->bytes), "stout graph workspace");
     if (st != LQ_OK) return st;
@@ -672,6 +687,7 @@ static lq_status run_graph(lq_field* f, double rho, int n, unsigned dirs, int re
     }
     it = graph_cache().emplace(k, e).first;
   }
+  it->second.used = now;
   return cuda_check(cudaGraphLaunch(it->second.exec, s), "stout graph launch");
 }
 

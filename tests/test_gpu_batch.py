@@ -54,3 +54,23 @@ def test_batch_rejects_mixed_precision_and_aliasing(gpu):
     with pytest.raises(lq.LqError) as e:
         lq.stout_smear_batch([a, a], 0.1, 1, SPATIAL)
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_cache_bounded_and_fresh_fields(gpu, graph):
+    """Many calls on fresh fields and new rho values (more distinct keys than
+    the graph cache keeps, so entries are evicted and rebuilt) stay equal to
+    separate calls bit for bit."""
+    import torch
+    dims_list = [(4, 4, 4, 8), (3, 5, 2, 7), (2, 2, 2, 2)]
+    rhos = [0.05 + 0.01 * k for k in range(6)]
+    for k, rho in enumerate(rhos):
+        Us = [fieldgen.near_identity_su3(d, 410 + 3 * k + i) for i, d in enumerate(dims_list)]
+        fields = [upload_links(U, lq.LQ_F32) for U in Us]
+        lq.stout_smear_batch(fields, rho, 3, SPATIAL, use_graph=graph, block=64, sites_per_thread=1)
+        for f, U in zip(fields, Us):
+            sep = upload_links(U, lq.LQ_F32)
+            lq.stout_smear(sep, rho, 3, SPATIAL)
+            assert np.array_equal(f.download(), sep.download()), (k, rho)
+        del fields
+        torch.cuda.synchronize()
