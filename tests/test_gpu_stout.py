@@ -2,10 +2,20 @@
 
 FP64 path: max |U_gpu - U_oracle| <= 1e-12 per link element (elements of SU(3)
 matrices are at most 1 in magnitude, so this is also the relative error with
-respect to the link).  FP32 path (FP32 matrix algebra, FP64 Cayley-Hamilton
-coefficients and re-projection): per-element error <= 2e-6 per step taken
-(FP32 rounding of ~3k operations per link, ~1e-7 each, accumulated over
-steps), unitarity <= 1e-6.
+respect to the link).
+
+FP32 path (FP32 matrix algebra, FP64 Cayley-Hamilton coefficients and
+re-projection), stated bound on the max per-element error against the exact
+(FP64) result, for up to 6 steps:
+  3e-7 on near-identity fields (exp(i 0.3 H)) up to 12^3 x 24,
+  4e-7 over the whole 48^3 x 96 lattice (4.2e8 elements: a larger maximum),
+  6e-7 on Haar-random fields (rho <= 0.4; links past the series domain).
+Measured on GB300 (3 seeds per case): 1.1e-7 .. 1.9e-7, 2.58e-7 and
+3.4e-7 .. 4.2e-7.  The error does not grow with the number of steps (48^3 x 96:
+2.43e-7 after 1 step, 2.58e-7 after 6): the input's own FP32 rounding
+(<= 4.2e-8) and each step's rounding are not amplified, since smearing is
+contractive and the FP64 re-projection holds every link on SU(3).
+Unitarity of FP32 results <= 1e-6.
 """
 import numpy as np
 import pytest
@@ -19,7 +29,8 @@ from tests.gpu_util import links_err, upload_links
 pytestmark = pytest.mark.gpu
 ALL, SPATIAL = (0, 1, 2, 3), (0, 1, 2)
 F64_TOL = 1e-12
-F32_TOL_PER_STEP = 2e-6
+F32_TOL = {"near": 3e-7, "haar": 6e-7}
+F32_TOL_48C96 = 4e-7
 
 
 def _run(U, prec, rho, n, dirs, **opts):
@@ -61,7 +72,7 @@ def test_f32_mixed_matches_oracle(gpu, dims, gen, rho, n, dirs):
     ref = stout.stout_smear(U, rho, n, dirs)
     got = _run(U, lq.LQ_F32, rho, n, dirs)
     a, _ = links_err(got, ref)
-    assert a <= F32_TOL_PER_STEP * n, a
+    assert a <= F32_TOL[gen], a
     du, dd = unitarity_violation(got.astype(np.complex128))
     assert du < 1e-6 and dd < 1e-6, (du, dd)
 
@@ -158,33 +169,43 @@ def test_16c32_ten_spatial_steps_f64(gpu):
     assert np.allclose(lq.plaquette(f), p_ref, rtol=0, atol=1e-13)
 
 
-@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
-def test_48c96_six_steps_sampled(gpu, prec):
+def test_48c96_six_steps(gpu):
     """48^3 x 96, exp(i 0.3 H) links, 6 steps rho = 0.125 in 4 dims, in the launch
-    configuration the benchmark uses; sampled sites are checked against the
+    configuration the benchmark uses.  FP64: 32 sampled sites against the
     oracle run on periodic boxes of side 13 around them (6 steps reach at most
-    6 sites in every direction, so the box centre is exact)."""
+    6 sites in every direction, so the box centre is exact).  FP32: every
+    element of the lattice against the FP64 result (compared on the device),
+    and the sampled sites against the oracle."""
     import torch
+    from tests.oracle_pool import stout_box_centers
     dims = (48, 48, 48, 96)
     n, rho = 6, 0.125
     Ut = fieldgen.near_identity_su3_torch(dims, 2, device="cuda")
     g = lq.Geometry(dims)
-    f = lq.Field(g, lq.LQ_LINKS, prec)
     U = Ut.cpu().numpy()
     del Ut
     torch.cuda.empty_cache()
-    f.upload(U)
-    lq.stout_smear(f, rho, n, ALL)
-    got = f.download()
+    f64 = lq.Field(g, lq.LQ_LINKS, lq.LQ_F64)
+    f64.upload(U)
+    lq.stout_smear(f64, rho, n, ALL)
+    f32 = lq.Field(g, lq.LQ_LINKS, lq.LQ_F32)
+    f32.upload(U)
+    lq.stout_smear(f32, rho, n, ALL)
+    worst_all = 0.0
+    for mu in range(4):   # |U32 - U64| per complex element, one direction at a time
+        d = (f32.tensor[mu].double() - f64.tensor[mu]).pow(2).sum(-1).sqrt()
+        worst_all = max(worst_all, float(d.max()))
+        del d
+    assert worst_all <= F32_TOL_48C96, worst_all
     rng = np.random.default_rng(5)
-    worst = 0.0
-    for _ in range(6):
-        c = [int(rng.integers(L)) for L in dims]
-        box = lattice.sub_box(U, c, n)
-        ref = stout.stout_smear(box, rho, n, ALL)[n, n, n, n]
-        worst = max(worst, float(np.max(np.abs(got[c[3], c[2], c[1], c[0]].astype(np.complex128) - ref))))
-    tol = F64_TOL if prec == lq.LQ_F64 else F32_TOL_PER_STEP * n
-    assert worst <= tol, worst
+    sites = [[int(rng.integers(L)) for L in dims] for _ in range(32)]
+    refs = stout_box_centers([lattice.sub_box(U, c, n) for c in sites], rho, n, ALL)
+    got64, got32 = f64.download(), f32.download()
+    w64 = max(float(np.max(np.abs(got64[c[3], c[2], c[1], c[0]] - r))) for c, r in zip(sites, refs))
+    w32 = max(float(np.max(np.abs(got32[c[3], c[2], c[1], c[0]].astype(np.complex128) - r)))
+              for c, r in zip(sites, refs))
+    assert w64 <= F64_TOL, w64
+    assert w32 <= F32_TOL_48C96, w32
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1, 1), (1, 2, 1, 3), (2, 1, 1, 1), (1, 1, 5, 1)])
@@ -309,7 +330,7 @@ def test_two_link_product_variant(gpu, dims, gen, rho, n, dirs):
     assert a <= F64_TOL and r <= F64_TOL, (a, r)
     assert np.max(np.abs(got - _run(U, lq.LQ_F64, rho, n, dirs, variant=1))) <= 1e-14
     got32 = _run(U, lq.LQ_F32, rho, n, dirs, variant=3)
-    assert np.max(np.abs(got32.astype(np.complex128) - ref)) <= F32_TOL_PER_STEP * n
+    assert np.max(np.abs(got32.astype(np.complex128) - ref)) <= F32_TOL[gen]
     for mu in range(4):
         if mu not in dirs:
             assert np.array_equal(got[..., mu, :, :], U[..., mu, :, :])
