@@ -411,6 +411,15 @@ typedef struct lq_jacobi_opts {
                              bytes) and rebuild row 2 = conj(row0 x row1); exact for
                              SU(3) links, to rounding for links unitary to
                              rounding; wrong for links outside SU(3).  0: off    */
+  int block;              /* N_threads ([W] Sec. 4.4): threads per block, a multiple
+                             of 32 in [32, 256]; 0 = tuned (lq_tune on) or 128   */
+  int sites_per_thread;   /* N_site ([W] Sec. 4.4): sites per thread in [1, 64];
+                             0 = tuned (lq_tune on) or 1.  With the tuner on and
+                             neither field set, the first call per (field kind,
+                             link storage, precision, dims, dirs, device) times
+                             N_threads in {32,64,128,256} x N_site in {1,2,4,8}
+                             on two iterations in its work buffers and keeps the
+                             fastest.  Any shape gives bit-identical results.   */
 } lq_jacobi_opts;
 
 /* lq_jacobi_smear with options (opts NULL => lq_jacobi_smear).  Compressed

@@ -330,13 +330,15 @@ def hyp_smear(links, a1=0.75, a2=0.6, a3=0.3, n_steps=1, stream=None):
 
 
 class LqJacobiOpts(ctypes.Structure):
-    _fields_ = [("struct_size", c_int), ("compress_links", c_int)]
+    _fields_ = [("struct_size", c_int), ("compress_links", c_int), ("block", c_int), ("sites_per_thread", c_int)]
 
 
-def jacobi_smear(links, chi, kappa, n_iter, norm=1.0, dirs=(0, 1, 2, 3), stream=None, compress_links=False):
+def jacobi_smear(links, chi, kappa, n_iter, norm=1.0, dirs=(0, 1, 2, 3), stream=None, compress_links=False,
+                 block=0, sites_per_thread=0):
     """In-place Jacobi smearing of a COLOR_VECTOR or FERMION field (Listing 1); compress_links
-    reads rows 0-1 of each link and rebuilds row 2 (lq_jacobi_smear_ex)."""
-    o = LqJacobiOpts(ctypes.sizeof(LqJacobiOpts), int(bool(compress_links)))
+    reads rows 0-1 of each link and rebuilds row 2; block / sites_per_thread set the thread
+    geometry N_threads / N_site (0: tuned or default) (lq_jacobi_smear_ex)."""
+    o = LqJacobiOpts(ctypes.sizeof(LqJacobiOpts), int(bool(compress_links)), int(block), int(sites_per_thread))
     _check(L.load().lq_jacobi_smear_ex(links.handle, chi.handle, float(kappa), int(n_iter), float(norm),
                                        dirs_mask(dirs), byref(o), _stream(stream)), "lq_jacobi_smear")
 

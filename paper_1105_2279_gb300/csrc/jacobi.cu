@@ -6,6 +6,8 @@
 //   chi'(x) = scale * (s0(x) + kappa * sum_mu [U_mu(x) chi(x+mu) + U_mu(x-mu)^dag chi(x-mu)])
 // with scale = 1/norm in the last iteration and 1 otherwise, for all spins of
 // a site at once (the links are read once per site).
+#include <cstddef>
+
 #include "lq_internal.h"
 #include "stout_core.cuh"
 
@@ -44,17 +46,17 @@ __global__ void k_pack12(const typename vec2<R>::type* __restrict__ U, typename 
   P[i] = U[(mu * 9 + c) * V + s];
 }
 
-template <typename R, int NSPIN, bool PACKED = false>
-__global__ void __launch_bounds__(128) k_jacobi(const typename vec2<R>::type* __restrict__ U,
-                                                const typename vec2<R>::type* __restrict__ chi,
-                                                const typename vec2<R>::type* __restrict__ s0,
-                                                typename vec2<R>::type* __restrict__ out, GeomArgs g, R kappa,
-                                                R scale, unsigned dirs) {
+// One site per (thread, k): a block of N_threads threads covers N_threads *
+// N_site consecutive sites, site k * N_threads + tid of its range in round k
+// (consecutive threads on consecutive sites in every round: coalesced).
+template <typename R, int NSPIN, bool PACKED>
+__device__ __forceinline__ void jacobi_site(const typename vec2<R>::type* __restrict__ U,
+                                            const typename vec2<R>::type* __restrict__ chi,
+                                            const typename vec2<R>::type* __restrict__ s0,
+                                            typename vec2<R>::type* __restrict__ out, const GeomArgs& g, R kappa,
+                                            R scale, unsigned dirs, int s) {
   typedef typename vec2<R>::type V2;
   const long long V = g.V;
-  const long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (sl >= V) return;
-  const int s = (int)sl;
   int c[4];
   site_coords(g, s, c);
   cx<R> h[NSPIN][3];
@@ -115,6 +117,20 @@ __global__ void __launch_bounds__(128) k_jacobi(const typename vec2<R>::type* __
     }
 }
 
+template <typename R, int NSPIN, bool PACKED = false>
+__global__ void __launch_bounds__(256) k_jacobi(const typename vec2<R>::type* __restrict__ U,
+                                                const typename vec2<R>::type* __restrict__ chi,
+                                                const typename vec2<R>::type* __restrict__ s0,
+                                                typename vec2<R>::type* __restrict__ out, GeomArgs g, R kappa,
+                                                R scale, unsigned dirs, int nsite) {
+  const long long base = (long long)blockIdx.x * blockDim.x * nsite + threadIdx.x;
+  for (int k = 0; k < nsite; ++k) {
+    const long long sl = base + (long long)k * blockDim.x;
+    if (sl >= g.V) return;
+    jacobi_site<R, NSPIN, PACKED>(U, chi, s0, out, g, kappa, scale, dirs, (int)sl);
+  }
+}
+
 template <typename R>
 __global__ void k_scale(typename vec2<R>::type* __restrict__ f, long long n, R scale) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -127,12 +143,14 @@ __global__ void k_scale(typename vec2<R>::type* __restrict__ f, long long n, R s
 
 template <typename R>
 static void launch_jacobi(int nspin, bool packed, const void* U, const void* in, const void* s0, void* out,
-                          const GeomArgs& g, double kappa, double scale, unsigned dirs, cudaStream_t s) {
+                          const GeomArgs& g, double kappa, double scale, unsigned dirs, const TuneChoice& tc,
+                          cudaStream_t s) {
   typedef typename vec2<R>::type V2;
-  const unsigned grid = (unsigned)((g.V + 127) / 128);
-#define LQ_J(NS, PK)                                                                                     \
-  k_jacobi<R, NS, PK><<<grid, 128, 0, s>>>((const V2*)U, (const V2*)in, (const V2*)s0, (V2*)out, g, (R)kappa, \
-                                           (R)scale, dirs)
+  const long long per_block = (long long)tc.block * tc.nsite;
+  const unsigned grid = (unsigned)((g.V + per_block - 1) / per_block);
+#define LQ_J(NS, PK)                                                                                          \
+  k_jacobi<R, NS, PK><<<grid, tc.block, 0, s>>>((const V2*)U, (const V2*)in, (const V2*)s0, (V2*)out, g, \
+                                                (R)kappa, (R)scale, dirs, tc.nsite)
   if (nspin == 4) {
     if (packed) LQ_J(4, true);
     else LQ_J(4, false);
@@ -141,6 +159,56 @@ static void launch_jacobi(int nspin, bool packed, const void* U, const void* in,
     else LQ_J(1, false);
   }
 #undef LQ_J
+}
+
+static lq_status launch_jacobi_prec(int prec, int nspin, bool packed, const void* U, const void* in, const void* s0,
+                                    void* out, const GeomArgs& g, double kappa, double scale, unsigned dirs,
+                                    const TuneChoice& tc, cudaStream_t s) {
+  if (prec == LQ_F64) launch_jacobi<double>(nspin, packed, U, in, s0, out, g, kappa, scale, dirs, tc, s);
+  else launch_jacobi<float>(nspin, packed, U, in, s0, out, g, kappa, scale, dirs, tc, s);
+  return launch_check("lq_jacobi_smear kernel");
+}
+
+// Tuner key of the Jacobi kernel: one entry per field kind and link storage.
+static const char* jacobi_kernel_key(int nspin, bool packed) {
+  if (nspin == 4) return packed ? "jacobi_fermion_packed" : "jacobi_fermion";
+  return packed ? "jacobi_vector_packed" : "jacobi_vector";
+}
+
+// The thread geometry of [W] Sec. 4.4 as the tuner's search space: every
+// N_threads in {32, 64, 128, 256} x N_site in {1, 2, 4, 8}, each timed on two
+// iterations into the work buffers (the caller's field is not touched).
+static lq_status jacobi_autotune(int prec, int nspin, bool packed, const void* U, const void* chi, void* w0, void* w1,
+                                 const GeomArgs& g, double kappa, unsigned dirs, cudaStream_t s, TuneChoice* best) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  lq_status st = LQ_OK;
+  const int blocks[] = {32, 64, 128, 256};
+  const int nsites[] = {1, 2, 4, 8};
+  for (int b : blocks)
+    for (int ns : nsites) {
+      TuneChoice c;
+      c.block = b;
+      c.nsite = ns;
+      c.variant = 1;
+      if ((st = launch_jacobi_prec(prec, nspin, packed, U, chi, chi, w0, g, kappa, 1.0, dirs, c, s))) break;
+      cudaEventRecord(e0, s);
+      launch_jacobi_prec(prec, nspin, packed, U, w0, chi, w1, g, kappa, 1.0, dirs, c, s);
+      launch_jacobi_prec(prec, nspin, packed, U, w1, chi, w0, g, kappa, 1.0, dirs, c, s);
+      cudaEventRecord(e1, s);
+      if ((st = cuda_check(cudaEventSynchronize(e1), "lq_jacobi_smear autotune timing"))) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        *best = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 }  // namespace lq
@@ -156,12 +224,23 @@ extern "C" lq_status lq_jacobi_smear_ex(const lq_field* links, lq_field* chi, do
                                         double norm, unsigned dirs_mask, const lq_jacobi_opts* opts,
                                         void* stream) {
   clear_error();
-  const lq_jacobi_opts* o = (opts && opts->struct_size >= (int)sizeof(lq_jacobi_opts)) ? opts : nullptr;
-  if (opts && !o && opts->struct_size != 0) {
-    set_error("lq_jacobi_smear: opts->struct_size %d < sizeof(lq_jacobi_opts)", opts->struct_size);
+  // fields past opts->struct_size read as 0 (callers built against the
+  // smaller struct without the launch-shape fields keep working)
+  const int osz = opts ? opts->struct_size : 0;
+  const int min_sz = (int)(offsetof(lq_jacobi_opts, compress_links) + sizeof(int));
+  if (opts && osz != 0 && osz < min_sz) {
+    set_error("lq_jacobi_smear: opts->struct_size %d too small", osz);
     return LQ_ERR_ARG;
   }
-  const bool packed = o && o->compress_links;
+  const bool packed = osz >= min_sz && opts->compress_links;
+  const int want_block = osz >= (int)(offsetof(lq_jacobi_opts, block) + sizeof(int)) ? opts->block : 0;
+  const int want_nsite =
+      osz >= (int)(offsetof(lq_jacobi_opts, sites_per_thread) + sizeof(int)) ? opts->sites_per_thread : 0;
+  if (want_block < 0 || want_block > 256 || (want_block % 32) != 0 || want_nsite < 0 || want_nsite > 64) {
+    set_error("lq_jacobi_smear: block must be a multiple of 32 in [32, 256] (0: tuned/default) and "
+              "sites_per_thread in [1, 64] (0: tuned/default)");
+    return LQ_ERR_ARG;
+  }
   lq_status st = check_links(links, "lq_jacobi_smear");
   if (st != LQ_OK) return st;
   if ((st = check_dirs(dirs_mask, "lq_jacobi_smear")) != LQ_OK) return st;
@@ -211,15 +290,30 @@ extern "C" lq_status lq_jacobi_smear_ex(const lq_field* links, lq_field* chi, do
       U = pk;
     }
   }
+  // thread geometry: explicit, else tuned (when the tuner is on), else 128 x 1
+  TuneChoice tc;
+  tc.block = 128;
+  tc.nsite = 1;
+  tc.variant = 1;
+  if (want_block > 0 || want_nsite > 0) {
+    if (want_block > 0) tc.block = want_block;
+    if (want_nsite > 0) tc.nsite = want_nsite;
+  } else if (st == LQ_OK && tune_enabled()) {
+    const char* key = jacobi_kernel_key(nspin, packed);
+    if (!tune_get(key, chi->prec, chi->geom.dims, dirs_mask, &tc)) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(s, &cs);
+      if (cs == cudaStreamCaptureStatusNone) {   // never tune inside a capture
+        st = jacobi_autotune(chi->prec, nspin, packed, U, chi->ptr, w[0], w[1], g, kappa, dirs_mask, s, &tc);
+        if (st == LQ_OK) tune_put(key, chi->prec, chi->geom.dims, dirs_mask, tc);
+      }
+    }
+  }
   const void* cur = chi->ptr;
   for (int it = 0; it < n_iter && st == LQ_OK; ++it) {
     void* out = w[it & 1];
     const double scale = (it == n_iter - 1) ? 1.0 / norm : 1.0;
-    if (chi->prec == LQ_F64)
-      launch_jacobi<double>(nspin, packed, U, cur, chi->ptr, out, g, kappa, scale, dirs_mask, s);
-    else
-      launch_jacobi<float>(nspin, packed, U, cur, chi->ptr, out, g, kappa, scale, dirs_mask, s);
-    st = launch_check("lq_jacobi_smear kernel");
+    st = launch_jacobi_prec(chi->prec, nspin, packed, U, cur, chi->ptr, out, g, kappa, scale, dirs_mask, tc, s);
     cur = out;
   }
   if (st == LQ_OK)

@@ -207,3 +207,25 @@ def test_field_checkpoint_header_checks(lqlib, tmp_path):
     assert b"differs" in lib.lq_last_error()
     assert lib.lq_field_load(h, str(tmp_path / "missing.lqf").encode(), None) == -1
     lib.lq_field_free(h)
+
+
+def test_jacobi_launch_shape_checked_before_device_work(lqlib):
+    """A thread geometry outside the tuner's range is refused with LQ_ERR_ARG
+    before any CUDA call (the fields point at unmapped addresses), and the
+    options struct of the previous, smaller layout is still accepted."""
+    from paper_1105_2279_gb300 import LqJacobiOpts
+    lib = lqlib.capi()
+    g = lqlib.Geometry((2, 2, 2, 2))
+    U, v = ctypes.c_void_p(), ctypes.c_void_p()
+    nU = lqlib.field_bytes(g, lqlib.LQ_LINKS, lqlib.LQ_F32)
+    nv = lqlib.field_bytes(g, lqlib.LQ_COLOR_VECTOR, lqlib.LQ_F32)
+    assert lib.lq_field_wrap(g.handle, lqlib.LQ_LINKS, lqlib.LQ_F32, ctypes.c_void_p(0x1000), nU, ctypes.byref(U)) == 0
+    assert lib.lq_field_wrap(g.handle, lqlib.LQ_COLOR_VECTOR, lqlib.LQ_F32, ctypes.c_void_p(0x100000), nv,
+                             ctypes.byref(v)) == 0
+    for block, nsite in ((48, 1), (512, 1), (-32, 1), (64, -1), (64, 65)):
+        o = LqJacobiOpts(ctypes.sizeof(LqJacobiOpts), 0, block, nsite)
+        assert lib.lq_jacobi_smear_ex(U, v, 0.1, 1, 1.0, 15, ctypes.byref(o), None) == -1, (block, nsite)
+        assert b"block" in lib.lq_last_error()
+    o = LqJacobiOpts(4, 0, 0, 0)       # struct_size below the first option
+    assert lib.lq_jacobi_smear_ex(U, v, 0.1, 1, 1.0, 15, ctypes.byref(o), None) == -1
+    assert lib.lq_field_free(U) == 0 and lib.lq_field_free(v) == 0

@@ -65,3 +65,43 @@ def test_jacobi_compressed_links(gpu, kind, prec, dims, n_iter, dirs):
     plain = lq.Field.from_host(fU.geom, k, prec, chi)
     lq.jacobi_smear(fU, plain, 0.21, n_iter, 1.7, dirs)
     assert np.max(np.abs(got - plain.download().astype(np.complex128))) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("kind", ["vector", "fermion"])
+@pytest.mark.parametrize("prec", [lq.LQ_F64, lq.LQ_F32])
+def test_jacobi_thread_geometry_bitwise(gpu, kind, prec):
+    """Every (N_threads, N_site) of the tuner's search space gives the default
+    launch's result bit for bit; the volume (5*3*7*9 = 945 sites) is a
+    multiple of no block size, so every shape has a ragged last block."""
+    dims = (5, 3, 7, 9)
+    U = fieldgen.haar_su3(dims, 620)
+    v = fieldgen.color_vector(dims, 621)
+    chi = v if kind == "vector" else np.stack([v, 0.5 * v[::-1], 1j * v, -v], axis=-2)
+    fU = upload_links(U, prec)
+    k = lq.LQ_COLOR_VECTOR if kind == "vector" else lq.LQ_FERMION
+    ref = lq.Field.from_host(fU.geom, k, prec, chi)
+    lq.jacobi_smear(fU, ref, 0.21, 3, 1.7)
+    want = ref.download()
+    for block in (32, 64, 128, 256):
+        for nsite in (1, 2, 4, 8):
+            f = lq.Field.from_host(fU.geom, k, prec, chi)
+            lq.jacobi_smear(fU, f, 0.21, 3, 1.7, block=block, sites_per_thread=nsite)
+            assert np.array_equal(f.download(), want), (block, nsite)
+
+
+def test_jacobi_tuner_picks_a_shape_and_keeps_results(gpu, tmp_path):
+    dims = (6, 6, 6, 12)
+    U = fieldgen.haar_su3(dims, 630)
+    v = fieldgen.color_vector(dims, 631)
+    fU = upload_links(U, lq.LQ_F32)
+    a = lq.Field.from_host(fU.geom, lq.LQ_COLOR_VECTOR, lq.LQ_F32, v)
+    lq.jacobi_smear(fU, a, 0.21, 4, 1.7)
+    cache = tmp_path / "tune.txt"
+    lq.tune(str(cache))
+    b = lq.Field.from_host(fU.geom, lq.LQ_COLOR_VECTOR, lq.LQ_F32, v)
+    lq.jacobi_smear(fU, b, 0.21, 4, 1.7)           # tunes, then smears with the chosen shape
+    assert np.array_equal(a.download(), b.download())
+    entries = [ln.split() for ln in cache.read_text().splitlines() if ln.startswith("jacobi_vector ")]
+    assert len(entries) == 1
+    block, nsite = int(entries[0][-3]), int(entries[0][-2])
+    assert block in (32, 64, 128, 256) and nsite in (1, 2, 4, 8)
