@@ -205,6 +205,16 @@ lq_status lq_reduce_trace(const lq_field* f, double out[2], void* stream);
  * Products in the field precision, accumulation in FP64.  Synchronises. */
 lq_status lq_plaquette(const lq_field* links, double out[3], void* stream);
 
+/* Unnormalised plaquette sums over the sites [s_begin, s_end) only:
+ * out[0] = sum of Re tr P over the 3 spatial planes, out[1] = over the 3
+ * temporal planes, products and accumulation as in lq_plaquette (fixed
+ * reduction tree for a given range size).  A rank of a domain-decomposed
+ * lattice sums its interior sites and the ranks add their sums (one FP64
+ * all-reduce of two numbers).  0 <= s_begin <= s_end <= volume.
+ * Synchronises. */
+lq_status lq_plaquette_sums(const lq_field* links, long long s_begin, long long s_end, double out[2],
+                            void* stream);
+
 /* Wilson action S = beta sum_x sum_{mu<nu} (1 - Re tr P_{mu nu}(x)/3). */
 lq_status lq_wilson_action(const lq_field* links, double beta, double* out, void* stream);
 
@@ -281,6 +291,21 @@ lq_status lq_stout_smear(lq_field* links_inout, double rho, int n_steps, unsigne
 lq_status lq_stout_smear_host(const void* host_in, void* host_out, const lq_geom* geom, int prec, double rho,
                               int n_steps, unsigned dirs_mask, int n_chunks, double* plaq_out,
                               const lq_stout_opts* opts, void* stream);
+
+/* One stout step from `in` into `out` over the sites [s_begin, s_end) only
+ * (site index x + Lx (y + Ly (z + Lz t))): for those sites and the
+ * directions in dirs_mask, out receives exactly the links lq_stout_smear's
+ * step would produce (same kernel and arithmetic, global-load variant; the
+ * launch shape from opts->block / sites_per_thread, else a cached tuning
+ * result, else the default); every other site and direction of out is left
+ * as it was.  This is the step of a domain-decomposed smearing ([W] Sec. 8
+ * names multi-GPU parallelisation as future work): a rank holding a slab of
+ * t-slices plus one halo slice on each side smears the slab's interior
+ * slices, whose staples read at most one slice away.  in and out: LINKS of
+ * one geometry and precision, distinct memory; 0 <= s_begin <= s_end <=
+ * volume; rho finite >= 0; dirs_mask in [1, 15].  Asynchronous. */
+lq_status lq_stout_step_range(const lq_field* in, lq_field* out, double rho, unsigned dirs_mask,
+                              long long s_begin, long long s_end, const lq_stout_opts* opts, void* stream);
 
 /* Coefficient-stage statistics of n_steps stout steps of `links` (which is
  * not modified; the steps run on library scratch copies with the default

@@ -239,6 +239,14 @@ def plaquette(links, stream=None):
     return (r[0], r[1], r[2])
 
 
+def plaquette_sums(links, s_begin, s_end, stream=None):
+    """Unnormalised (spatial, temporal) Re tr P sums over the sites [s_begin, s_end)."""
+    r = (c_double * 2)()
+    _check(L.load().lq_plaquette_sums(links.handle, int(s_begin), int(s_end), r, _stream(stream)),
+           "lq_plaquette_sums")
+    return (r[0], r[1])
+
+
 def wilson_action(links, beta, stream=None):
     r = c_double()
     _check(L.load().lq_wilson_action(links.handle, float(beta), byref(r), _stream(stream)), "lq_wilson_action")
@@ -262,6 +270,13 @@ def stout_smear(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None, **opts):
     o = stout_opts(**opts)
     _check(L.load().lq_stout_smear(links.handle, float(rho), int(n_steps), dirs_mask(dirs), byref(o),
                                    _stream(stream)), "lq_stout_smear")
+
+
+def stout_step_range(inp, out, rho, s_begin, s_end, dirs=(0, 1, 2, 3), stream=None, **opts):
+    """One stout step from `inp` into `out` over the sites [s_begin, s_end) (lq_stout_step_range)."""
+    o = stout_opts(**opts)
+    _check(L.load().lq_stout_step_range(inp.handle, out.handle, float(rho), dirs_mask(dirs), int(s_begin),
+                                        int(s_end), byref(o), _stream(stream)), "lq_stout_step_range")
 
 
 def stout_smear_noalloc(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
@@ -310,6 +325,7 @@ def stout_ch_stats(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
     _check(L.load().lq_stout_ch_stats(links.handle, float(rho), int(n_steps), dirs_mask(dirs), c,
                                       _stream(stream)), "lq_stout_ch_stats")
     return int(c[0]), int(c[1]), int(c[2])
+
 
 
 def expiq(out, q, stream=None):

@@ -55,6 +55,7 @@ SIGNATURES = {
     "lq_reduce_sum": (c_int, [_P, POINTER(c_double), _P]),
     "lq_reduce_trace": (c_int, [_P, POINTER(c_double), _P]),
     "lq_plaquette": (c_int, [_P, POINTER(c_double), _P]),
+    "lq_plaquette_sums": (c_int, [_P, c_longlong, c_longlong, POINTER(c_double), _P]),
     "lq_wilson_action": (c_int, [_P, c_double, POINTER(c_double), _P]),
     "lq_stout_smear": (c_int, [_P, c_double, c_int, c_uint, POINTER(LqStoutOpts), _P]),
     "lq_stout_backward": (c_int, [_P, c_double, c_int, c_uint, _P, c_double, _P, _P, POINTER(LqBackwardOpts), _P]),
@@ -69,6 +70,7 @@ SIGNATURES = {
     "lq_hyp_smear": (c_int, [_P, c_double, c_double, c_double, c_int, _P]),
     "lq_expiq": (c_int, [_P, _P, _P]),
     "lq_stout_ch_stats": (c_int, [_P, c_double, c_int, c_uint, _P, _P]),
+    "lq_stout_step_range": (c_int, [_P, _P, c_double, c_uint, c_longlong, c_longlong, POINTER(LqStoutOpts), _P]),
     "lq_stout_smear_host": (c_int, [_P, _P, _P, c_int, c_double, c_int, c_uint, c_int, _P, _P, _P]),
     "lq_tune": (c_int, [ctypes.c_char_p]),
     "lq_tune_lookup": (c_int, [c_int, POINTER(c_int), c_uint, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),

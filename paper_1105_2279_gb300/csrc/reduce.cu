@@ -9,12 +9,14 @@ namespace lq {
 
 // Re tr P_{mu nu}(x) = Re tr[(U_mu(x) U_nu(x+mu)) (U_nu(x) U_mu(x+nu))^dag],
 // summed over the spatial planes (nu < 3) and the temporal planes (nu = 3).
+// Sites [s0, s1) (the whole lattice, or the slab a rank owns).
 template <typename R>
 __global__ void __launch_bounds__(kReduceThreads) k_plaquette(const typename vec2<R>::type* __restrict__ U,
-                                                              GeomArgs g, double* __restrict__ parts) {
+                                                              GeomArgs g, long long s0, long long s1,
+                                                              double* __restrict__ parts) {
   double v[2] = {0.0, 0.0};
   const long long V = g.V;
-  for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < V;
+  for (long long sl = s0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < s1;
        sl += (long long)gridDim.x * blockDim.x) {
     const int s = (int)sl;
     int c[4];
@@ -95,15 +97,20 @@ static lq_status reduce_two(int grid, cudaStream_t s, double out[2], const char*
   return st;
 }
 
-lq_status plaquette_sums(const lq_field* links, double out_planes[2], cudaStream_t s) {
+static lq_status plaquette_sums_range(const lq_field* links, long long s0, long long s1, double out_planes[2],
+                                      cudaStream_t s) {
   const GeomArgs g = geom_args(links->geom);
-  const int grid = reduce_grid(g.V);
+  const int grid = reduce_grid(s1 - s0);
   return reduce_two(grid, s, out_planes, "lq_plaquette", [&](double* parts) {
     if (links->prec == LQ_F64)
-      k_plaquette<double><<<grid, kReduceThreads, 0, s>>>((const double2*)links->ptr, g, parts);
+      k_plaquette<double><<<grid, kReduceThreads, 0, s>>>((const double2*)links->ptr, g, s0, s1, parts);
     else
-      k_plaquette<float><<<grid, kReduceThreads, 0, s>>>((const float2*)links->ptr, g, parts);
+      k_plaquette<float><<<grid, kReduceThreads, 0, s>>>((const float2*)links->ptr, g, s0, s1, parts);
   });
+}
+
+lq_status plaquette_sums(const lq_field* links, double out_planes[2], cudaStream_t s) {
+  return plaquette_sums_range(links, 0, links->geom.volume, out_planes, s);
 }
 
 }  // namespace lq
@@ -126,6 +133,22 @@ extern "C" lq_status lq_plaquette(const lq_field* links, double out[3], void* st
   out[1] = sums[0] / (9.0 * V);
   out[2] = sums[1] / (9.0 * V);
   return LQ_OK;
+}
+
+extern "C" lq_status lq_plaquette_sums(const lq_field* links, long long s_begin, long long s_end, double out[2],
+                                       void* stream) {
+  clear_error();
+  lq_status st = check_links(links, "lq_plaquette_sums");
+  if (st != LQ_OK) return st;
+  if (!out || s_begin < 0 || s_end < s_begin || s_end > links->geom.volume) {
+    set_error("lq_plaquette_sums: need an output and 0 <= s_begin <= s_end <= volume");
+    return LQ_ERR_ARG;
+  }
+  if (s_end == s_begin) {
+    out[0] = out[1] = 0.0;
+    return LQ_OK;
+  }
+  return plaquette_sums_range(links, s_begin, s_end, out, as_stream(stream));
 }
 
 extern "C" lq_status lq_wilson_action(const lq_field* links, double beta, double* out, void* stream) {

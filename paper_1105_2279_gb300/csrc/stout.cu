@@ -808,6 +808,44 @@ extern "C" lq_status lq_stout_smear(lq_field* links, double rho, int n_steps, un
   return st;
 }
 
+extern "C" lq_status lq_stout_step_range(const lq_field* in, lq_field* out, double rho, unsigned dirs_mask,
+                                         long long s_begin, long long s_end, const lq_stout_opts* opts,
+                                         void* stream) {
+  clear_error();
+  lq_status st = check_links(in, "lq_stout_step_range");
+  if (st != LQ_OK) return st;
+  if ((st = check_links(out, "lq_stout_step_range")) != LQ_OK) return st;
+  if ((st = check_dirs(dirs_mask, "lq_stout_step_range")) != LQ_OK) return st;
+  if (out->prec != in->prec || !same_geom(out->geom, in->geom)) {
+    set_error("lq_stout_step_range: in and out must share geometry and precision");
+    return LQ_ERR_GEOM;
+  }
+  if (out->ptr == in->ptr) {
+    set_error("lq_stout_step_range: out must not alias in");
+    return LQ_ERR_ARG;
+  }
+  if (!(rho >= 0.0) || rho > 1e6 || s_begin < 0 || s_end < s_begin || s_end > in->geom.volume) {
+    set_error("lq_stout_step_range: need finite rho >= 0 and 0 <= s_begin <= s_end <= volume");
+    return LQ_ERR_ARG;
+  }
+  if (s_end == s_begin) return LQ_OK;
+  const lq_stout_opts* o = (opts && opts->struct_size >= (int)sizeof(lq_stout_opts)) ? opts : nullptr;
+  const int reproject = (o && o->reproject >= 0) ? o->reproject : (in->prec == LQ_F32 ? 1 : 0);
+  TuneChoice tc = stout_default_choice(in->prec);
+  if (o && o->block > 0) {
+    if (o->block % 32 != 0 || o->block > 256) {
+      set_error("lq_stout_step_range: block must be a multiple of 32 in [32, 256]");
+      return LQ_ERR_ARG;
+    }
+    tc.block = o->block;
+    tc.nsite = o->sites_per_thread > 0 ? o->sites_per_thread : 1;
+  } else if (tune_enabled()) {
+    tune_get("stout", in->prec, in->geom.dims, dirs_mask, &tc);
+  }
+  return stout_step_range(in->ptr, out->ptr, in->geom, in->prec, rho, dirs_mask, reproject, tc, s_begin, s_end,
+                          as_stream(stream));
+}
+
 extern "C" lq_status lq_stout_ch_stats(const lq_field* links, double rho, int n_steps, unsigned dirs_mask,
                                        long long* counts, void* stream) {
   clear_error();
