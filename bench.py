@@ -203,6 +203,60 @@ def time_oracle_sample(n_steps=1, dims=(16, 16, 16, 32)):
     return links / dt, dt, links
 
 
+def _pool_noop(i):
+    return i
+
+
+def _oracle_slab_step(task):
+    """One FP64 oracle stout step of the t-slices [t0, t1) of a lattice held in
+    shared memory: the slab plus one halo slice on each side is smeared as a
+    lattice of its own (a step reads neighbours one slice away, so its
+    interior slices are exact) and the interior is written to the output."""
+    from multiprocessing import shared_memory
+    from oracle import stout
+    name_in, name_out, shape, t0, t1 = task
+    a, b = shared_memory.SharedMemory(name=name_in), shared_memory.SharedMemory(name=name_out)
+    try:
+        U = np.ndarray(shape, dtype=np.complex128, buffer=a.buf)
+        out = np.ndarray(shape, dtype=np.complex128, buffer=b.buf)
+        slab = U[[t % shape[0] for t in range(t0 - 1, t1 + 1)]]
+        out[t0:t1] = stout.stout_step(slab, RHO, DIRS)[1:-1]
+        del U, out
+    finally:
+        a.close()
+        b.close()
+    return t1 - t0
+
+
+def time_oracle_all_cores(U):
+    """The FP64 oracle's stout step on all host cores: t-slabs (one per core,
+    each with a one-slice halo) in a spawned process pool over shared memory.
+    Returns (link-updates/s, seconds, link updates, processes)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    procs = os.cpu_count() or 1
+    Lt = U.shape[0]
+    per = -(-Lt // procs)
+    tasks_t = [(t0, min(Lt, t0 + per)) for t0 in range(0, Lt, per)]
+    a = shared_memory.SharedMemory(create=True, size=U.nbytes)
+    b = shared_memory.SharedMemory(create=True, size=U.nbytes)
+    try:
+        np.ndarray(U.shape, dtype=np.complex128, buffer=a.buf)[...] = U
+        tasks = [(a.name, b.name, U.shape, t0, t1) for t0, t1 in tasks_t]
+        with mp.get_context("spawn").Pool(processes=procs) as pool:
+            pool.map(_pool_noop, range(procs))      # start-up, not timed
+            t0 = time.perf_counter()
+            pool.map(_oracle_slab_step, tasks, chunksize=1)
+            dt = time.perf_counter() - t0
+    finally:
+        a.close()
+        a.unlink()
+        b.close()
+        b.unlink()
+    links = int(np.prod(U.shape[:4])) * len(DIRS)
+    return links / dt, dt, links, procs
+
+
 def run_reference(args, rank):
     """The oracle as the reference arm: each step a bounded sample (one stout step on 12^3 x 24)."""
     if rank != 0:
@@ -231,6 +285,49 @@ def run_reference(args, rank):
     print(json.dumps(out), flush=True)
 
 
+def _compact_roof(r, probe):
+    keep = {k: r[k] for k in ("bound", "pipe", "unit", "achieved", "peak", "frac", "fp64_flops_per_link")
+            if k in r}
+    if probe and "achieved" in r:
+        keep["frac_of_measured_fp64"] = r["achieved"] / probe["fp64_tflops"]
+    return keep
+
+
+def run_secondary(sargs, torch, lq, fieldgen, bw, probe):
+    """The 64-lattice batch, the 24^3x48 gradient and the 16^3x32 micro-suite,
+    each as a compact object of the headline line (value, time, roofline,
+    accuracy against the oracle or finite differences)."""
+    out = {}
+    t0 = time.perf_counter()
+    b = bw.batch64(sargs, torch, lq, fieldgen)
+    out["batch64"] = {"value": b["value"], "unit": b["unit"], "ms_per_step": b["ms_per_step"], "dtype": "f32",
+                      "config": b["config"]["workload"], "separate_calls": b["separate_calls"],
+                      "persistent_no_graph": b["persistent_no_graph"],
+                      "speedup_vs_separate": b["speedup_vs_separate"],
+                      "roofline": _compact_roof(b["roofline"], probe), "accuracy": b["accuracy"]}
+    torch.cuda.empty_cache()
+    g = bw.backward24(sargs, torch, lq, fieldgen)
+    bk = {"metric": g["metric"], "unit": g["unit"], "config": g["config"]["workload"]}
+    for prec in ("f64", "f32"):
+        r = g[prec]
+        bk[prec] = {"value": r["checkpoint_every_1"]["value"], "ms": r["checkpoint_every_1"]["ms"],
+                    "recompute_every_3_ms": r["checkpoint_every_3"]["ms"],
+                    "roofline": _compact_roof(r["roofline"], probe), "forward_ms": r["forward_ms"]}
+        if "fd_max_rel" in r:
+            bk[prec]["fd_max_rel"] = r["fd_max_rel"]
+            bk[prec]["fd_config"] = r["fd_config"]
+    bk["accuracy"] = g.get("accuracy")
+    out["backward24"] = bk
+    torch.cuda.empty_cache()
+    m = bw.micro16(sargs, torch, lq, fieldgen)
+    out["micro16"] = {"value": m["value"], "unit": m["unit"], "ms_per_step": m["ms_per_step"], "dtype": "f64",
+                      "config": m["config"]["workload"], "micro_suite_ms": m["micro_suite_ms"],
+                      "accuracy": m["accuracy"]}
+    torch.cuda.empty_cache()
+    out["secondary_wall_s"] = time.perf_counter() - t0
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -238,8 +335,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the batch, gradient and micro-suite objects of the headline line")
+    ap.add_argument("--fd-links", type=int, default=4, help="finite-difference links of the gradient check")
     ap.add_argument("--f64-steps", type=int, default=3)
     ap.add_argument("--dims", default=None, help="Lx,Ly,Lz,Lt override (smaller profiling cases)")
+    ap.add_argument("--prec", default="both", choices=["both", "f32", "f64"],
+                    help="secondary workloads with an FP32 and an FP64 leg: run only one of them")
     ap.add_argument("--variant", type=int, default=0,
                     help="step kernel: 0 auto-tuned (default), 1 global loads, 2 shared-memory staged (FP32)")
     ap.add_argument("--workload", default="stout48",
@@ -403,11 +505,34 @@ def main():
     e2e_same = bool(np.array_equal(out_pipelined, pin_out.numpy()))
     del out_pipelined
 
+    # measured FMA throughput of the two pipes (the rooflines' measured denominators)
+    probe = {"fp64_tflops": lq.peak_probe(lq.LQ_F64), "fp32_tflops": lq.peak_probe(lq.LQ_F32),
+             "how": "lq_peak_probe: 8 CTAs x 256 threads per SM, 8 independent FMA chains per thread, CUDA events"}
+
+    # secondary configurations (64-lattice batch, 24^3x48 gradient, 16^3x32 micro-suite)
+    h2d_bytes, d2h_bytes = int(pin_in.numel() * 4), int(pin_out.numel() * 4)
+    del f32, f64, pin_in, pin_out
+    torch.cuda.empty_cache()
+    secondary = {}
+    if rank == 0 and not args.no_secondary:
+        import types
+        import bench_workloads
+        sargs = types.SimpleNamespace(steps=max(1, min(args.steps, 5)), warmup=max(3, args.warmup), dims=None,
+                                      prec="both", fd_links=args.fd_links)
+        secondary = run_secondary(sargs, torch, lq, fieldgen, bench_workloads, probe)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, n = time_oracle_sample()
+        Ua = fieldgen.near_identity_su3_torch((24, 24, 24, 96), SEED, device="cuda").cpu().numpy()
+        torch.cuda.empty_cache()
+        va, dta, na, procs = time_oracle_all_cores(Ua)
+        del Ua
         cpu = {"value": v, "unit": "link-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"1 FP64 stout step, 4 dirs, on 16^3x32 (same generator and rho): {n} link updates in {dt:.1f} s"}
+               "sample": f"1 FP64 stout step, 4 dirs, on 16^3x32 (same generator and rho): {n} link updates in {dt:.1f} s",
+               "all_cores": {"value": va, "unit": "link-updates/s", "cores": procs, "kind": "oracle",
+                             "sample": f"1 FP64 stout step, 4 dirs, on 24^3x96 as {procs} t-slabs with one-slice "
+                                       f"halos in a spawned process pool: {na} link updates in {dta:.2f} s"}}
 
     if rank == 0:
         value = weak_scaling_value(links_per_step, world, step32 * 1e-3)
@@ -451,7 +576,7 @@ def main():
                          "fp64_vs_oracle_sampled_max_abs": e64o, "plaquette_fp32": p32[0], "plaquette_fp64": p64[0],
                          "plaquette_abs_diff": abs(p32[0] - p64[0])},
             "e2e": {"value": weak_scaling_value(links_per_step, world, e2e_ms * 1e-3), "unit": "link-updates/s",
-                    "h2d_bytes_per_step": int(pin_in.numel() * 4), "d2h_bytes_per_step": int(pin_out.numel() * 4),
+                    "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
                     "ms_per_step": e2e_ms, "statistic": "median over the timed calls", "ms_mean": e2e_mean,
                     "ms_calls": e2e_calls,
                     "call": "lq_stout_smear_host (16 t-slabs, transfers overlapped)",
@@ -462,7 +587,11 @@ def main():
             "gpu_launches": args.steps * (N_SMEAR + 2),
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "peaks_measured": probe,
         }
+        out["roofline"]["frac_of_measured_fp64"] = roof32["achieved"] / probe["fp64_tflops"]
+        out["fp64"]["roofline"]["frac_of_measured_fp64"] = roof64["achieved"] / probe["fp64_tflops"]
+        out.update(secondary)
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.barrier()

@@ -52,6 +52,13 @@ def _dims(args, default):
     return tuple(int(x) for x in args.dims.split(",")) if args.dims else default
 
 
+def _precs(args, lq):
+    """The (name, precision) legs to run: both by default, or the one --prec names."""
+    legs = (("f64", lq.LQ_F64), ("f32", lq.LQ_F32))
+    want = getattr(args, "prec", "both")
+    return [leg for leg in legs if want in ("both", leg[0])]
+
+
 def _field(lq, fieldgen, dims, seed, prec, device="cuda"):
     import torch
     U = fieldgen.near_identity_su3_torch(dims, seed, device=device).cpu().numpy()
@@ -59,12 +66,20 @@ def _field(lq, fieldgen, dims, seed, prec, device="cuda"):
     return lq.Field.from_host(lq.Geometry(dims), lq.LQ_LINKS, prec, U), U
 
 
+def _fp64_peak_tflops():
+    import bench
+    return 2.0 * bench.FP64_FMA_PER_CLK * 2070.0 * 1e6 / 1e12
+
+
 def batch64(args, torch, lq, fieldgen):
+    import bench
+    from oracle import stout
     Ls = fieldgen.batch_sizes(3, 64)
     fields = []
     for i, L in enumerate(Ls):
         f, _ = _field(lq, fieldgen, (L, L, L, 2 * L), 3 + i, lq.LQ_F32)
         fields.append(f)
+    orig = [f.tensor.clone() for f in fields]
     sites = sum(2 * L ** 4 for L in Ls)
     links = 6 * sites * 3
     dirs = (0, 1, 2)
@@ -75,6 +90,29 @@ def batch64(args, torch, lq, fieldgen):
         for f in fields:
             lq.stout_smear(f, 0.1, 6, dirs)
     t_sep = _events(torch, separate, args.steps, args.warmup)
+    # FP64 work of the coefficient stage on these inputs (series orders per link)
+    tot = [0, 0, 0]
+    for f, o in zip(fields, orig):
+        f.tensor.copy_(o)
+        st = lq.stout_ch_stats(f, 0.1, 6, dirs)
+        tot = [a + b for a, b in zip(tot, st)]
+    f64_flops = bench.ch_flops_per_link(tot) + bench.REPROJECT_FLOPS_PER_LINK
+    peak = _fp64_peak_tflops()
+    achieved = f64_flops * links / (t_graph * 1e-3) / 1e12
+    # accuracy: one graph-replayed batch call against separate calls (bit for bit) and,
+    # for the smallest lattice, against the FP64 oracle on the FP32-rounded input
+    lq.stout_smear_batch(fields, 0.1, 6, dirs, use_graph=True)
+    equal = True
+    for f, o in zip(fields, orig):
+        sep = lq.Field(f.geom, lq.LQ_LINKS, lq.LQ_F32)
+        sep.tensor.copy_(o)
+        lq.stout_smear(sep, 0.1, 6, dirs)
+        equal = equal and bool(torch.equal(sep.tensor, f.tensor))
+    i0 = int(np.argmin(Ls))
+    src = lq.Field(fields[i0].geom, lq.LQ_LINKS, lq.LQ_F32)
+    src.tensor.copy_(orig[i0])
+    ref = stout.stout_smear(src.download().astype(np.complex128), 0.1, 6, dirs)
+    err = float(np.max(np.abs(fields[i0].download().astype(np.complex128) - ref)))
     return {"metric": "stout link-updates/s (batch of 64 uneven lattices)", "value": links / (t_graph * 1e-3),
             "unit": "link-updates/s", "ms_per_step": t_graph, "dtype": "f32",
             "config": {"workload": "64 x L^3x2L, L in {8,12,16,20,24} seed 3, 6 spatial steps rho=0.1",
@@ -82,7 +120,63 @@ def batch64(args, torch, lq, fieldgen):
             "persistent_no_graph": {"value": links / (t_plain * 1e-3), "ms_per_step": t_plain},
             "separate_calls": {"value": links / (t_sep * 1e-3), "ms_per_step": t_sep,
                                "launches_per_step": 64 * 6},
-            "speedup_vs_separate": t_sep / t_graph}
+            "speedup_vs_separate": t_sep / t_graph,
+            "roofline": {"bound": "alu", "pipe": "fp64", "unit": "TFLOP/s", "achieved": achieved, "peak": peak,
+                         "frac": achieved / peak, "fp64_flops_per_link": f64_flops,
+                         "peak_source": f"derived: {bench.FP64_FMA_PER_CLK} FP64 FMA/clk x 2 x 2070 MHz",
+                         "ch_stats": tot},
+            "accuracy": {"equal_to_separate_calls": equal,
+                         "fp32_vs_oracle_max_abs": err,
+                         "oracle_config": f"L={Ls[i0]} (config {i0}), FP64 oracle on the FP32-rounded input"}}
+
+
+def _plane_diff_programs():
+    """Per plane: Re tr P(operand 0) - Re tr P(operand 1) per site (the action
+    difference of two fields formed before the sum over sites)."""
+    progs = []
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            p = []
+            for k, r0 in ((0, 0), (1, 4)):
+                p += [("loadl", r0, k, mu, 0, 0), ("loadl", r0 + 1, k, nu, mu, +1), ("mul", r0, r0, r0 + 1),
+                      ("loadl", r0 + 1, k, nu, 0, 0), ("loadl", r0 + 2, k, mu, nu, +1),
+                      ("mul", r0 + 1, r0 + 1, r0 + 2), ("adj", r0 + 1, r0 + 1), ("mul", r0, r0, r0 + 1),
+                      ("retr", r0, r0)]
+            p += [("sub", 0, 0, 4), ("store", 0)]
+            progs.append(p)
+    return progs
+
+
+def backward_fd(lq, fieldgen, thin, F, rho, n, beta, n_links, eps=1e-4, seed=44):
+    """Central finite differences of the smeared Wilson action along random
+    unit su(3) directions at n_links random links (FP64 links on the device),
+    against the force F (host array); returns the max relative difference."""
+    from scipy.linalg import expm
+    import torch
+    g = thin.geom
+    dims = g.dims
+    fp, fm = lq.Field(g, lq.LQ_LINKS, lq.LQ_F64), lq.Field(g, lq.LQ_LINKS, lq.LQ_F64)
+    progs = _plane_diff_programs()
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(n_links):
+        mu = int(rng.integers(4))
+        c = [int(rng.integers(L)) for L in dims]
+        s = c[0] + dims[0] * (c[1] + dims[1] * (c[2] + dims[2] * c[3]))
+        X = fieldgen.su3_direction(rng)
+        t = thin.tensor[mu, :, s, :].cpu().numpy()
+        u = (t[:, 0] + 1j * t[:, 1]).reshape(3, 3)
+        an = float(np.real(np.trace(F[c[3], c[2], c[1], c[0], mu].conj().T @ X)))
+        for fld, sign in ((fp, 1.0), (fm, -1.0)):
+            fld.tensor.copy_(thin.tensor)
+            w = (expm(sign * eps * X) @ u).reshape(9)
+            fld.tensor[mu, :, s, 0] = torch.from_numpy(w.real.copy()).to(fld.tensor.device)
+            fld.tensor[mu, :, s, 1] = torch.from_numpy(w.imag.copy()).to(fld.tensor.device)
+            lq.stout_smear(fld, rho, n, (0, 1, 2, 3))
+        d_retr = sum(lq.expr_eval(p, [fp, fm], reduce=True).real for p in progs) / 3.0
+        fd = -(beta / 3.0) * d_retr / (2 * eps)
+        worst = max(worst, abs(fd - an) / max(1.0, abs(an)))
+    return worst
 
 
 # Algorithmic flops per link of the backward (4 smeared directions), counted
@@ -106,8 +200,8 @@ def backward24(args, torch, lq, fieldgen):
     n, rho = 3, 0.1
     out = {"metric": "stout force link-updates/s (3 steps, Wilson action)", "unit": "link-updates/s",
            "config": {"workload": f"{'x'.join(map(str, dims))}, exp(i*0.3*H) links seed 4, 3 stout steps rho=0.1 in 4 dims, beta=6"}}
-    pk = bench.peaks()
-    for name, prec in (("f64", lq.LQ_F64), ("f32", lq.LQ_F32)):
+    forces = {}
+    for name, prec in _precs(args, lq):
         f, _ = _field(lq, fieldgen, dims, 4, prec)
         F = lq.Field(f.geom, lq.LQ_LINKS, prec)
         stats = lq.stout_ch_stats(f, rho, n, (0, 1, 2, 3))
@@ -143,12 +237,25 @@ def backward24(args, torch, lq, fieldgen):
                            "mean_series_order_fp64_table": mean_k, "mean_series_order_own_table": own_k,
                            "note": "checkpoint_every=1; flops of the forward recompute included"}
         g = lq.Field(f.geom, lq.LQ_LINKS, prec)
-        g.tensor.copy_(f.tensor)
-        tf = _events(torch, lambda: lq.stout_smear(g, 0.1, 3, (0, 1, 2, 3)), args.steps, args.warmup)
-        res["forward_ms"] = tf
+
+        def fwd():
+            g.tensor.copy_(f.tensor)   # the same input every call (smearing in place smooths it)
+            lq.stout_smear(g, 0.1, 3, (0, 1, 2, 3))
+        res["forward_ms"] = _events(torch, fwd, args.steps, args.warmup)
+        res["forward_ms_note"] = "3 steps from the thin links, including a links-sized device copy per call"
+        lq.stout_backward(f, rho, n, (0, 1, 2, 3), F, beta=6.0)
+        forces[name] = F.download()
+        if name == "f64" and getattr(args, "fd_links", 4) > 0:
+            res["fd_max_rel"] = backward_fd(lq, fieldgen, f, forces[name], rho, n, 6.0, args.fd_links)
+            res["fd_config"] = f"central differences, step 1e-4, at {args.fd_links} random links (seed 44)"
         out[name] = res
-    out["value"] = out["f64"]["checkpoint_every_1"]["value"]
-    out["dtype"] = "f64"
+    if "f32" in forces and "f64" in forces:
+        scale = float(np.max(np.abs(forces["f64"])))
+        out["accuracy"] = {"fp32_vs_fp64_force_max_rel": float(np.max(np.abs(
+            forces["f32"].astype(np.complex128) - forces["f64"]))) / scale}
+    first = "f64" if "f64" in out else "f32"
+    out["value"] = out[first]["checkpoint_every_1"]["value"]
+    out["dtype"] = first
     return out
 
 
@@ -191,6 +298,47 @@ def jacobi32(args, torch, lq, fieldgen):
                     "ms": t, "gflops": flops / (t * 1e-3) / 1e9, "gb_s": total / (t * 1e-3) / 1e9,
                     "hbm_frac": total / (t * 1e-3) / 1e9 / hbm}
         out[name] = res
+    # thread geometry of Sec. 4.4 (the paper's Figs. 1-2 axes N_threads, N_site), FP32
+    # colour vector on 32^3 x 64: every shape of the tuner's search space
+    dims = (32, 32, 32, 64)
+    V = int(np.prod(dims))
+    fU, _ = _field(lq, fieldgen, dims, 5, lq.LQ_F32)
+    chi = lq.Field(fU.geom, lq.LQ_COLOR_VECTOR, lq.LQ_F32)
+    chi.tensor.normal_()
+    flops = JACOBI_FLOPS_PER_SPIN * V * n_iter
+    sweep = {}
+    for block in (32, 64, 128, 256):
+        for nsite in (1, 2, 4, 8):
+            t = _events(torch, lambda: lq.jacobi_smear(fU, chi, 0.21, n_iter, 1.0, block=block,
+                                                       sites_per_thread=nsite), args.steps, args.warmup)
+            sweep[f"{block}x{nsite}"] = {"ms": t, "gflops": flops / (t * 1e-3) / 1e9}
+    best = max(sweep, key=lambda k: sweep[k]["gflops"])
+    out["thread_geometry_f32_32c64_vector"] = {"shapes": sweep, "best": best,
+                                               "default_128x1_gflops": sweep["128x1"]["gflops"]}
+    del fU, chi
+    torch.cuda.empty_cache()
+    # the lattices of the paper's Table 1, tuned launch shape, colour vector
+    lq.tune(None)
+    table = {}
+    paper = {"8^3x16": (1.64, 1.49), "12^3x24": (6.53, 4.41), "16^3x32": (11.86, 6.26), "20^3x40": (16.56, 7.51),
+             "24^3x48": (19.09, 7.91), "32^3x64": (21.31, None)}
+    for L in (8, 12, 16, 20, 24, 32):
+        dims = (L, L, L, 2 * L)
+        V = int(np.prod(dims))
+        row = {}
+        for name, prec in (("f32", lq.LQ_F32), ("f64", lq.LQ_F64)):
+            if L == 32 and prec == lq.LQ_F64:
+                continue
+            fU, _ = _field(lq, fieldgen, dims, 5, prec)
+            chi = lq.Field(fU.geom, lq.LQ_COLOR_VECTOR, prec)
+            chi.tensor.normal_()
+            t = _events(torch, lambda: lq.jacobi_smear(fU, chi, 0.21, n_iter, 1.0), args.steps, args.warmup)
+            row[name + "_gflops"] = JACOBI_FLOPS_PER_SPIN * V * n_iter / (t * 1e-3) / 1e9
+        key = f"{L}^3x{2 * L}"
+        row["paper_gtx480_sp_gflops"], row["paper_gtx480_dp_gflops"] = paper[key]
+        table[key] = row
+    out["table1_lattices"] = {"rows": table, "note": "colour vector, 20 iterations, tuned N_threads x N_site; the "
+                                                      "paper's numbers are its whole routine on a GTX 480 (context)"}
     out["value"] = out["f32_32c64"]["vector"]["gflops"]
     out["dtype"] = "f32"
     return out
@@ -379,7 +527,25 @@ def micro16(args, torch, lq, fieldgen):
     t_tr_jit = _events(torch, lambda: lq.expr_eval_jit(p_tr, [f], reduce=True), args.steps, args.warmup)
     t_adj_jit = _events(torch, lambda: lq.expr_eval_jit(p_adj, [f], out=out), args.steps, args.warmup)
     links = 10 * V * 3
+    # accuracy against the oracle: spatial smearing never leaves a time slice
+    # (staples over x, y, z only), so the oracle on single slices (periodic
+    # 16^3 x 1 lattices) is exact for them; the micro-suite sums on the whole field
+    from oracle import expr as oexpr, gauge, stout
+    g.tensor.copy_(f.tensor)
+    lq.stout_smear(g, 0.1, 10, (0, 1, 2))
+    got = g.download()
+    e_smear = 0.0
+    for t in (0, 17):
+        ref = stout.stout_smear(U[t:t + 1], 0.1, 10, (0, 1, 2))
+        e_smear = max(e_smear, float(np.max(np.abs(got[t:t + 1] - ref))))
+    tr_gpu = lq.expr_eval(p_tr, [f], reduce=True)
+    tr_ref = oexpr.trace_sum(oexpr.eval_program(p_tr, [U]))
+    plaq_ref = gauge.plaquette(U)[0]
+    accuracy = {"smear_vs_oracle_max_abs": e_smear, "smear_oracle_sample": "time slices t=0 and t=17 (exact)",
+                "trace_sum_rel": abs(tr_gpu - tr_ref) / abs(tr_ref),
+                "plaquette_abs": abs(lq.plaquette(f)[0] - plaq_ref)}
     return {"metric": "stout link-updates/s (16^3x32, 10 spatial steps, FP64)", "value": links / (t_smear * 1e-3),
+            "accuracy": accuracy,
             "unit": "link-updates/s", "ms_per_step": t_smear, "dtype": "f64",
             "config": {"workload": "16^3x32, exp(i*0.3*H) links seed 1, 10 stout steps rho=0.1 spatial"},
             "micro_suite_ms": {"trace_sum_mu_tr_UU_shift": t_tr, "shifted_adjoint_product": t_adj,

@@ -492,6 +492,17 @@ lq_status lq_tune(const char* cache_path);
 lq_status lq_tune_lookup(int prec, const int dims[4], unsigned dirs_mask, int* block,
                          int* sites_per_thread, int* variant);
 
+/* ---- measurement ---------------------------------------------------------- */
+
+/* CUDA-core FMA throughput of the current device, measured: a grid of 8 CTAs
+ * of 256 threads per SM, each thread running eight independent FMA chains in
+ * precision prec (LQ_F32 or LQ_F64), one untimed launch and one timed with
+ * CUDA events on `stream` (~20 ms).  *tflops receives 2 x FMAs / time in
+ * TFLOP/s: the measured peak of the FP32 and FP64 pipes, the denominators of
+ * the rooflines of kernels bound by them.  The paper has no counterpart.
+ * Synchronizes the stream. */
+lq_status lq_peak_probe(int prec, double* tflops, void* stream);
+
 /* Releases every cache the library holds on the device (workspaces, graphs,
  * descriptor tables), like theDeviceStorage::freeAll() ([W] Sec. 5).
  * Fields are not touched. */

@@ -327,6 +327,12 @@ def stout_ch_stats(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
     return int(c[0]), int(c[1]), int(c[2])
 
 
+def peak_probe(prec, stream=None):
+    """Measured FMA throughput of the FP32 or FP64 pipe in TFLOP/s (lq_peak_probe)."""
+    t = c_double()
+    _check(L.load().lq_peak_probe(int(prec), byref(t), _stream(stream)), "lq_peak_probe")
+    return t.value
+
 
 def expiq(out, q, stream=None):
     """out = exp(iQ) per site (Cayley-Hamilton, FP64 coefficients) of a COLOR_MATRIX field."""

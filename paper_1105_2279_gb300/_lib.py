@@ -72,6 +72,7 @@ SIGNATURES = {
     "lq_stout_ch_stats": (c_int, [_P, c_double, c_int, c_uint, _P, _P]),
     "lq_stout_step_range": (c_int, [_P, _P, c_double, c_uint, c_longlong, c_longlong, POINTER(LqStoutOpts), _P]),
     "lq_stout_smear_host": (c_int, [_P, _P, _P, c_int, c_double, c_int, c_uint, c_int, _P, _P, _P]),
+    "lq_peak_probe": (c_int, [c_int, POINTER(c_double), _P]),
     "lq_tune": (c_int, [ctypes.c_char_p]),
     "lq_tune_lookup": (c_int, [c_int, POINTER(c_int), c_uint, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
     "lq_free_all": (c_int, []),
