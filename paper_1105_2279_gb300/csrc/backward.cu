@@ -50,19 +50,33 @@ __device__ __forceinline__ M3<R> ld(const V2<R>* __restrict__ F, long long V, in
   return ld_m3<R>(F + (long long)dir * 9 * V + s, V);
 }
 
-// Link stage of a stout step for the smeared link (s, mu): G' the gradient at
-// U'_mu(x); returns G_U(local) in gl and K in kk.
+// Link stage of a stout step for the smeared link (s, mu), in two parts: the
+// prefix recomputes the step's staple sum, Q and the FP64 coefficients with
+// their derivatives (independent of the incoming gradient), the rest takes
+// G' = the gradient at U'_mu(x) and returns G_U(local) in gl and K in kk.
+template <typename R> struct StoutLinkPre {
+  M3<R> C;
+  QH<R> q;
+  CHDeriv d;
+};
+
 template <typename R>
-__device__ __forceinline__ void stout_link_grad(const V2<R>* __restrict__ U, const GeomArgs& g, int s,
-                                                const int c[4], int mu, unsigned dirs, R rho, const M3<R>& Gpm,
-                                                M3<R>& gl, M3<R>& kk) {
-  const long long V = g.V;
-  const M3<R> C = m_rscale(staple_sum<R, true>(U, g, s, c, mu, dirs), rho);
-  const M3<R> Umu = ld<R>(U, V, mu, s);
-  const QH<R> q = q_from_omega(mul_nd(C, Umu));
-  const CHDeriv d = ch_coefficients_deriv<sizeof(R) == 4 ? 1 : 2>(
+__device__ __forceinline__ void stout_link_pre(const V2<R>* __restrict__ U, const GeomArgs& g, int s, const int c[4],
+                                               int mu, unsigned dirs, R rho, StoutLinkPre<R>& p) {
+  p.C = m_rscale(staple_sum<R, true>(U, g, s, c, mu, dirs), rho);
+  const QH<R> q = q_from_omega(mul_nd(p.C, ld<R>(U, g.V, mu, s)));
+  p.q = q;
+  p.d = ch_coefficients_deriv<sizeof(R) == 4 ? 1 : 2>(
       to_f64(q.d0), to_f64(q.d1), to_f64(q.d2), mkc(to_f64(q.o01.re), to_f64(q.o01.im)),
       mkc(to_f64(q.o02.re), to_f64(q.o02.im)), mkc(to_f64(q.o12.re), to_f64(q.o12.im)));
+}
+
+template <typename R>
+__device__ __forceinline__ void stout_link_rest(const V2<R>* __restrict__ U, const GeomArgs& g, int s, int mu, R rho,
+                                                const StoutLinkPre<R>& p, const M3<R>& Gpm, M3<R>& gl, M3<R>& kk) {
+  const QH<R>& q = p.q;
+  const CHDeriv& d = p.d;
+  const M3<R> Umu = ld<R>(U, g.V, mu, s);
   const QH<R> q2 = q_square(q);
   const M3<R> Qf = qh_full(q), Q2f = qh_full(q2);
   const M3<R> GE = mul_nd(Gpm, Umu);  // G_E = G' U^dag
@@ -92,7 +106,7 @@ __device__ __forceinline__ void stout_link_grad(const V2<R>* __restrict__ U, con
   // E = exp(iQ) and the local gradient E^dag G' + G_Omega^dag C
   const M3<R> E = expiq_assemble(q, q2, mkc<R>(from_f64<R>(d.f[0].re), from_f64<R>(d.f[0].im)), f1, f2);
   gl = mul_dn(E, Gpm);
-  mac_dn(gl, GO, C);
+  mac_dn(gl, GO, p.C);
   kk = m_rscale(mul_nn(GO, Umu), rho);
 }
 
@@ -194,26 +208,32 @@ __global__ void __launch_bounds__(128) k_bwd_step(BwdArgs<R> p) {
   const long long off = (long long)a * 9 * V + s;
   int c[4];
   site_coords(g, s, c);
+  const bool smeared = (p.dirs >> a) & 1u;
   // G' = G at U^(j+1) for the link (s, a)
   M3<R> Gp;
   if (SRC == kSrcWilson) {
     Gp = m_rscale(staple_sum<R, true>(p.Unext, g, s, c, a, 15u), p.mbeta3);
   } else {
     Gp = ld_m3<R>(p.Gin + off, V);
-    if (SRC == kSrcGather && ((p.dirs >> a) & 1u)) staple_gather<R>(p.Unext, p.Knext, g, s, c, a, p.dirs, Gp);
+    if (SRC == kSrcGather && smeared) staple_gather<R>(p.Unext, p.Knext, g, s, c, a, p.dirs, Gp);
   }
   if (DST == kDstFinal) {
     if (p.Gout) st_m3<R>(p.Gout + off, V, Gp);
     if (p.Fout) st_m3<R>(p.Fout + off, V, m_ta(mul_nd(Gp, ld_m3<R>(p.Ucur + off, V))));
     return;
   }
-  if (!((p.dirs >> a) & 1u)) {  // not smeared: the gradient passes through
+  if (!smeared) {  // not smeared: the gradient passes through
     st_m3<R>(p.Gout + off, V, Gp);
     return;
   }
   M3<R> gl, kk;
-  if (DST == kDstStout) stout_link_grad<R>(p.Ucur, g, s, c, a, p.dirs, p.w0, Gp, gl, kk);
-  else ape_link_grad<R>(p.Ucur, g, s, c, a, p.dirs, p.w0, p.w1, Gp, gl, kk);
+  if (DST == kDstStout) {
+    StoutLinkPre<R> pre;
+    stout_link_pre<R>(p.Ucur, g, s, c, a, p.dirs, p.w0, pre);
+    stout_link_rest<R>(p.Ucur, g, s, a, p.w0, pre, Gp, gl, kk);
+  } else {
+    ape_link_grad<R>(p.Ucur, g, s, c, a, p.dirs, p.w0, p.w1, Gp, gl, kk);
+  }
   st_m3<R>(p.Gout + off, V, gl);
   st_m3<R>(p.Kout + off, V, kk);
 }

@@ -60,11 +60,12 @@ __device__ __forceinline__ void stout_global_body(const typename vec2<R>::type* 
   }
 }
 
-// FP32 links: capped at 72 registers (no spills), which fits 28 resident
-// warps per SM for blocks of 64 or 128 threads instead of 24: more warps to
-// keep the FP64 pipe, the step's bottleneck, fed.
+// FP32 links: capped at 80 registers (16 bytes of spill), 24 resident warps
+// per SM for blocks of 128 or 256 threads: measured against 72 (28 warps,
+// 168 bytes of spill) and 96 (20 warps, none) at 48^3x96, 8.08 ms per step
+// against 8.14 and 8.33.
 template <bool REPRO, bool COUNT = false>
-__global__ void __maxnreg__(72) k_stout_global_f32(const float2* __restrict__ Uin, float2* __restrict__ Uout,
+__global__ void __maxnreg__(80) k_stout_global_f32(const float2* __restrict__ Uin, float2* __restrict__ Uout,
                                                    GeomArgs g, float rho, unsigned dirs, int nsite, int nd,
                                                    MuList ml, unsigned long long* stats, int s_begin, int s_end) {
   stout_global_body<float, REPRO, COUNT>(Uin, Uout, g, rho, dirs, nsite, nd, ml, stats, s_begin, s_end, blockIdx.x);
