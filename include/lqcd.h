@@ -102,11 +102,15 @@ lq_status lq_field_device_ptr(const lq_field* f, void** ptr_out);
 
 /* Host AoS -> device SoA ([W] Sec. 5 pushToLattice copy).  host_aos holds
  * lq_field_bytes() bytes in the host interchange layout; it is read before
- * the call returns (the stream is synchronised).  Pinned host memory makes
- * the copy asynchronous-capable and faster. */
+ * the call returns (the stream is synchronised).  Page-locked host memory
+ * (cudaHostAlloc / cudaHostRegister, which the GPU addresses directly) is
+ * read by the transpose kernel itself over the host link; pageable memory
+ * is copied into a device staging buffer first. */
 lq_status lq_field_upload(lq_field* f, const void* host_aos, void* stream);
 
-/* Device SoA -> host AoS ([W] Sec. 5 popFromLattice copy); synchronises. */
+/* Device SoA -> host AoS ([W] Sec. 5 popFromLattice copy); page-locked host
+ * memory is written by the transpose kernel directly, pageable memory through
+ * a staging buffer and a copy.  Synchronises. */
 lq_status lq_field_download(const lq_field* f, void* host_aos, void* stream);
 
 /* Field checkpoints on disk (checkpoint / resume of smeared fields).  File:

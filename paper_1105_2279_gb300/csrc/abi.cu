@@ -233,6 +233,15 @@ static lq_status transpose(const void* src, void* dst, const lq_field* f, bool t
   return transpose_range(src, dst, f->geom, f->kind, f->prec, to_soa, 0, f->geom.volume, s);
 }
 
+void* host_device_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 }  // namespace lq
 
 using namespace lq;
@@ -381,6 +390,11 @@ lq_status lq_field_upload(lq_field* f, const void* host_aos, void* stream) {
     return LQ_ERR_ARG;
   }
   cudaStream_t s = as_stream(stream);
+  if (const void* dv = host_device_view(host_aos)) {   // page-locked: the transpose reads it directly
+    lq_status st = transpose(dv, f->ptr, f, true, s);
+    lq_status st2 = cuda_check(cudaStreamSynchronize(s), "lq_field_upload sync");
+    return st != LQ_OK ? st : st2;
+  }
   void* stage = nullptr;
   lq_status st = scratch_alloc(&stage, f->bytes, s, "lq_field_upload");
   if (st != LQ_OK) return st;
@@ -398,6 +412,11 @@ lq_status lq_field_download(const lq_field* f, void* host_aos, void* stream) {
     return LQ_ERR_ARG;
   }
   cudaStream_t s = as_stream(stream);
+  if (void* dv = host_device_view(host_aos)) {   // page-locked: the transpose writes it directly
+    lq_status st = transpose(f->ptr, dv, f, false, s);
+    lq_status st2 = cuda_check(cudaStreamSynchronize(s), "lq_field_download sync");
+    return st != LQ_OK ? st : st2;
+  }
   void* stage = nullptr;
   lq_status st = scratch_alloc(&stage, f->bytes, s, "lq_field_download");
   if (st != LQ_OK) return st;

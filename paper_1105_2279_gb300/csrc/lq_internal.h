@@ -134,6 +134,9 @@ lq_status stout_step_segments(const StepSegment* seg, int nseg, const lq_geom& g
 // between a whole-lattice AoS buffer and a whole-lattice SoA buffer.
 lq_status transpose_range(const void* src, void* dst, const lq_geom& g, int kind, int prec, bool to_soa,
                           long long s_begin, long long s_end, cudaStream_t s);
+// The device address of page-locked host memory (the GPU reads and writes it
+// over the host link), or NULL for memory the GPU cannot address directly.
+void* host_device_view(const void* p);
 lq_status stout_choose(const lq_field* f, double rho, unsigned dirs, int reproject,
                        const lq_stout_opts* o, cudaStream_t s, TuneChoice* out);
 

@@ -9,9 +9,11 @@ namespace lq {
 
 // Re tr P_{mu nu}(x) = Re tr[(U_mu(x) U_nu(x+mu)) (U_nu(x) U_mu(x+nu))^dag],
 // summed over the spatial planes (nu < 3) and the temporal planes (nu = 3).
-// Sites [s0, s1) (the whole lattice, or the slab a rank owns).
+// Sites [s0, s1) (the whole lattice, or the slab a rank owns).  FP32 links:
+// held to 128 registers, two 256-thread blocks per SM (at the 130 it would
+// take unbounded, one block of 8 warps per SM left the loads' latency bare).
 template <typename R>
-__global__ void __launch_bounds__(kReduceThreads) k_plaquette(const typename vec2<R>::type* __restrict__ U,
+__global__ void __launch_bounds__(kReduceThreads, sizeof(R) == 4 ? 2 : 1) k_plaquette(const typename vec2<R>::type* __restrict__ U,
                                                               GeomArgs g, long long s0, long long s1,
                                                               double* __restrict__ parts) {
   double v[2] = {0.0, 0.0};

@@ -103,7 +103,7 @@ __device__ __forceinline__ void stout_seg_body(const SegList& sg, GeomArgs g, R 
 }
 
 template <bool REPRO>
-__global__ void __maxnreg__(72) k_stout_seg_f32(SegList sg, GeomArgs g, float rho, unsigned dirs, int nsite, int nd,
+__global__ void __maxnreg__(80) k_stout_seg_f32(SegList sg, GeomArgs g, float rho, unsigned dirs, int nsite, int nd,
                                                 MuList ml) {
   stout_seg_body<float, REPRO>(sg, g, rho, dirs, nsite, nd, ml);
 }

@@ -31,6 +31,29 @@ def test_upload_download_roundtrip(gpu, prec):
     assert t[2, 5, s, 1] == want[4, 1, 3, 1, 2, 1, 2].imag
 
 
+@pytest.mark.parametrize("kind,prec", [(lq.LQ_LINKS, lq.LQ_F64), (lq.LQ_LINKS, lq.LQ_F32),
+                                       (lq.LQ_FERMION, lq.LQ_F32), (lq.LQ_REAL, lq.LQ_F64)])
+def test_pinned_upload_download_equal_pageable(gpu, kind, prec):
+    """From page-locked host memory the transposes read and write the host
+    buffer themselves (no staging copy): the same bytes as the pageable path
+    (staging copy, then transpose); ragged volume, several field kinds."""
+    import torch
+    dims = (3, 5, 7, 11)
+    g = lq.Geometry(dims)
+    a = lq.Field(g, kind, prec)
+    rng = np.random.default_rng(210)
+    real = np.float64 if prec == lq.LQ_F64 else np.float32
+    host = rng.standard_normal(a.nbytes // np.dtype(real).itemsize).astype(real)
+    pinned = torch.from_numpy(host.copy()).pin_memory()
+    a.upload_ptr(host.ctypes.data)
+    b = lq.Field(g, kind, prec)
+    b.upload_ptr(pinned.data_ptr())
+    assert torch.equal(a.tensor, b.tensor)
+    out = torch.zeros_like(pinned).pin_memory()
+    b.download_ptr(out.data_ptr())
+    assert np.array_equal(out.numpy(), host)
+
+
 @pytest.mark.parametrize("dims,gen", [((4, 4, 4, 4), "haar"), ((2, 2, 2, 2), "near"),
                                       ((3, 4, 5, 6), "near"), ((8, 8, 8, 16), "near")])
 def test_plaquette(gpu, dims, gen):

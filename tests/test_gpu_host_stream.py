@@ -112,10 +112,27 @@ def test_host_stream_trace_respects_dependencies(gpu, tmp_path, monkeypatch, n):
     for i in range(nc):
         nb = ((i - 1) % nc, i, (i + 1) % nc)
         assert t[("to_soa", i, 0)][0] >= t[("h2d", i, 0)][1] - eps
+        assert t[("d2h", i, n)][0] >= t[("to_aos", i, n)][1] - eps
         for j in nb:
             assert t[("step", i, 1)][0] >= t[("to_soa", j, 0)][1] - eps
         for k in range(2, n + 1):
             if k not in whole:
                 assert t[("step", i, k)][0] >= end_of(k - 1, nb) - eps
         assert t[("to_aos", i, n)][0] >= t[("step", i, n)][1] - eps
-        assert t[("d2h", i, n)][0] >= t[("to_aos", i, n)][1] - eps
+
+
+@pytest.mark.parametrize("prec", [lq.LQ_F32, lq.LQ_F64])
+def test_host_stream_pinned_16_slabs(gpu, prec):
+    """Page-locked buffers, 16 slabs over 6 steps: bit-identical to the
+    device path."""
+    import torch
+    dims = (2, 3, 4, 32)
+    U = fieldgen.near_identity_su3(dims, 703)
+    ref, p_ref = _reference(U, prec, 0.125, 6, ALL)
+    h = _host(U, prec)
+    fl = np.float32 if prec == lq.LQ_F32 else np.float64
+    hin = torch.from_numpy(h.view(fl).copy()).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    p = lq.stout_smear_host(hin, hout, dims, prec, 0.125, 6, ALL)
+    assert np.array_equal(hout.numpy().view(h.dtype).reshape(h.shape), ref)
+    assert p == tuple(p_ref)
