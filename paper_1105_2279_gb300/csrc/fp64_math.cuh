@@ -16,8 +16,10 @@ namespace lq {
 // integer pipe (the hardware conversions issue on the FP64 pipe, which is the
 // bottleneck).  f2d: exact for normal numbers and zero (FP32 subnormals become
 // signed zero, inf/NaN keep their class).  d2f: round to nearest, ties to
-// even, for results in the FP32 normal range; anything else (zero, tiny,
-// huge, inf, NaN) takes the hardware conversion.
+// even, for results in the FP32 normal range; below it signed zero (FP32
+// subnormals flushed), above it infinity, NaN kept.  No branch and no
+// hardware conversion: a fallback to the hardware conversion, even one that
+// no lane takes, is issued to the FP64 pipe by the whole warp.
 __device__ __forceinline__ double f2d(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xffu;
@@ -28,11 +30,13 @@ __device__ __forceinline__ double f2d(float f) {
 }
 __device__ __forceinline__ float d2f(double d) {
   const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;
-  if (e <= 0 || e >= 255) return __double2float_rn(d);
-  unsigned f = (hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned sign = hi & 0x80000000u, mag = hi & 0x7fffffffu;
+  const int e = (int)(mag >> 20) - 896;
+  unsigned f = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
   const unsigned rest = lo & 0x1fffffffu;
-  f += (rest > 0x10000000u ? 1u : 0u) | (rest == 0x10000000u ? (f & 1u) : 0u);
+  f += (rest > 0x10000000u ? 1u : 0u) | (rest == 0x10000000u ? (f & 1u) : 0u);   // a carry may reach inf
+  const bool nan = mag > 0x7ff00000u || (mag == 0x7ff00000u && lo != 0u);
+  f = e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u | (nan ? 0x00400000u : 0u)) : f);
   return __uint_as_float(f);
 }
 

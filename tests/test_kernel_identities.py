@@ -160,3 +160,43 @@ def test_fp32_derivative_series_order_is_enough():
             e2 = max(abs(b2[j] - B2[j]) * q ** j for j in range(3)) * 3.0 * q * q
             worst = max(worst, e1, e2)
     assert worst <= 2.3e-10, worst
+
+
+def _d2f_bits(d):
+    """numpy restatement of the kernels' integer-pipe double -> float
+    conversion (IEEE-754 bit fields, round to nearest even; signed zero
+    below the FP32 normal range, infinity above it, NaN kept)."""
+    b = np.asarray(d, dtype=np.float64).view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.uint64)
+    lo = (b & np.uint64(0xffffffff)).astype(np.uint64)
+    sign = hi & np.uint64(0x80000000)
+    mag = hi & np.uint64(0x7fffffff)
+    e = (mag >> np.uint64(20)).astype(np.int64) - 896
+    f = sign | (np.clip(e, 0, 255).astype(np.uint64) << np.uint64(23)) | ((hi & np.uint64(0xfffff)) << np.uint64(3)) \
+        | (lo >> np.uint64(29))
+    rest = lo & np.uint64(0x1fffffff)
+    f = f + np.where(rest > 0x10000000, 1, np.where(rest == 0x10000000, f & np.uint64(1), 0)).astype(np.uint64)
+    nan = (mag > 0x7ff00000) | ((mag == 0x7ff00000) & (lo != 0))
+    f = np.where(e <= 0, sign, np.where(e >= 255, sign | np.uint64(0x7f800000) | np.where(nan, 0x400000, 0).astype(np.uint64), f))
+    return (f & np.uint64(0xffffffff)).astype(np.uint32).view(np.float32)
+
+
+def test_integer_double_to_float_conversion():
+    """The conversion equals numpy's (IEEE round to nearest even) over the
+    FP32 normal range, including exact ties and carries into the exponent,
+    and gives zero / infinity / NaN outside it."""
+    rng = np.random.default_rng(77)
+    d = np.concatenate([rng.standard_normal(200000) * 10.0 ** rng.integers(-30, 30, 200000),
+                        rng.standard_normal(1000)])
+    # exact ties between two floats, both parities, and values that round up to the next binade
+    f = rng.standard_normal(1000).astype(np.float32)
+    up = np.nextafter(f, np.float32(np.inf))
+    d = np.concatenate([d, 0.5 * (f.astype(np.float64) + up.astype(np.float64)),
+                        [np.float64(np.nextafter(np.float32(2.0), np.float32(0))) + 2.0 ** -26,
+                         1.0, -1.0, 3.4028234663852886e38, 1.1754943508222875e-38]])
+    assert np.array_equal(_d2f_bits(d).view(np.uint32), d.astype(np.float32).view(np.uint32))
+    special = np.array([0.0, -0.0, 1e-39, -1e-45, 1e-300, 4e38, -1e300, np.inf, -np.inf, np.nan])
+    got = _d2f_bits(special)
+    assert np.array_equal(got[:5].view(np.uint32), np.array([0, 0x80000000, 0, 0x80000000, 0], dtype=np.uint32))
+    assert got[5] == np.inf and got[6] == -np.inf and got[7] == np.inf and got[8] == -np.inf
+    assert np.isnan(got[9])
