@@ -4,10 +4,13 @@ Cayley-Hamilton coefficients and re-projection) beside FP64.
 Workload: 48^3 x 96 periodic lattice (10,616,832 sites), links exp(i 0.3 H)
 with H random traceless Hermitian (seeded), 6 stout steps rho = 0.125 in all
 4 directions followed by the FP64-accumulated plaquette.  One bench step =
-that whole sequence on device-resident links (each step smears the previous
-step's output in place; the arithmetic per link does not depend on the
-values).  The 3 GB (FP32) / 6 GB (FP64) link fields are far larger than the
-129 MB L2, so no L2 flush is needed between steps.
+that whole sequence on device-resident links; every step smears the same thin
+links, restored by a device copy before the step and outside its CUDA-event
+interval (the Cayley-Hamilton coefficients' series order, and with it the
+FP64 work per link, falls as a field gets smoother: smearing the previous
+output again would time an easier workload).  The 3 GB (FP32) / 6 GB (FP64)
+link fields are far larger than the 129 MB L2, so no L2 flush is needed
+between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -397,29 +400,33 @@ def main():
             dist.barrier()
 
     def timed(field, steps, warmup, opts=None):
+        """Mean time of one bench step (6 smearing steps + plaquette).  Every step smears
+        the same input: the links are restored from a device copy before each step,
+        outside its timed interval (the coefficient series' order, and with it a
+        step's FP64 work, falls as the field gets smoother, so smearing the previous
+        output again would time an easier workload)."""
         field.upload(U_host)
+        orig = field.tensor.clone()
         if opts is None:
             opts = smear_opts if field.prec == lq.LQ_F32 or args.variant != 2 else {}
         for _ in range(warmup):
+            field.tensor.copy_(orig)
             lq.stout_smear(field, RHO, N_SMEAR, DIRS, **opts)
             lq.plaquette(field)
         barrier()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        t_all0 = torch.cuda.Event(enable_timing=True)
-        t_all1 = torch.cuda.Event(enable_timing=True)
-        t_all0.record(stream)
         for e0, e1, e2 in ev:
+            field.tensor.copy_(orig)
             e0.record(stream)
             lq.stout_smear(field, RHO, N_SMEAR, DIRS, **opts)   # N_SMEAR launches of the fused step kernel
             e1.record(stream)
             lq.plaquette(field)                          # 2 launches, synchronises
             e2.record(stream)
-        t_all1.record(stream)
         barrier()
-        total_ms = t_all0.elapsed_time(t_all1)
+        step_ms = max_over_ranks(float(np.sum([a.elapsed_time(c) for a, _, c in ev])) / steps, dist)
         smear_ms = [a.elapsed_time(b) for a, b, _ in ev]
-        step_ms = max_over_ranks(total_ms / steps, dist)
+        del orig
         return step_ms, float(np.mean(smear_ms)) / N_SMEAR
 
     pk = peaks()
@@ -563,7 +570,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "precision": "FP32 matrix algebra and storage; FP64 Cayley-Hamilton coefficients, SU(3) re-projection and plaquette accumulation",
             "config": {"workload": WORKLOAD, "lattice": list(DIMS), "n_smear": N_SMEAR, "rho": RHO, "dirs": "xyzt",
-                       "l2": "inputs larger than L2 (3.06 GB FP32 links)", "per_rank": "independent lattice per rank"},
+                       "l2": "inputs larger than L2 (3.06 GB FP32 links)", "per_rank": "independent lattice per rank",
+                       "input_per_step": "the same thin links every step, restored by a device copy outside the step's CUDA-event interval"},
             "roofline": roof32,
             "fp64": {"value": value64, "ms_per_step": step64, "kernel_ms": kern64, "roofline": roof64},
             "fp64_two_link_products": {

@@ -34,17 +34,34 @@ import json
 import numpy as np
 
 
-def _events(torch, fn, steps, warmup):
+def _events(torch, fn, steps, warmup, reset=None):
+    """Mean CUDA-event time of fn over `steps` calls after `warmup` calls; with
+    `reset`, the inputs are restored before every call, outside its interval
+    (smearing in place smooths a field, and a smoother field takes less FP64
+    work in the coefficient series)."""
     for _ in range(warmup):
+        if reset:
+            reset()
         fn()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    if reset is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+    total = 0.0
     for _ in range(steps):
+        reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         fn()
-    e1.record()
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / steps
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
 
 
 def _dims(args, default):
@@ -83,13 +100,18 @@ def batch64(args, torch, lq, fieldgen):
     sites = sum(2 * L ** 4 for L in Ls)
     links = 6 * sites * 3
     dirs = (0, 1, 2)
-    t_graph = _events(torch, lambda: lq.stout_smear_batch(fields, 0.1, 6, dirs, use_graph=True), args.steps, args.warmup)
-    t_plain = _events(torch, lambda: lq.stout_smear_batch(fields, 0.1, 6, dirs), args.steps, args.warmup)
+    def restore():
+        for f, o in zip(fields, orig):
+            f.tensor.copy_(o)
+    t_graph = _events(torch, lambda: lq.stout_smear_batch(fields, 0.1, 6, dirs, use_graph=True), args.steps,
+                      args.warmup, reset=restore)
+    t_plain = _events(torch, lambda: lq.stout_smear_batch(fields, 0.1, 6, dirs), args.steps, args.warmup,
+                      reset=restore)
 
     def separate():
         for f in fields:
             lq.stout_smear(f, 0.1, 6, dirs)
-    t_sep = _events(torch, separate, args.steps, args.warmup)
+    t_sep = _events(torch, separate, args.steps, args.warmup, reset=restore)
     # FP64 work of the coefficient stage on these inputs (series orders per link)
     tot = [0, 0, 0]
     for f, o in zip(fields, orig):
@@ -240,11 +262,9 @@ def backward24(args, torch, lq, fieldgen):
                            "note": "checkpoint_every=1; flops of the forward recompute included"}
         g = lq.Field(f.geom, lq.LQ_LINKS, prec)
 
-        def fwd():
-            g.tensor.copy_(f.tensor)   # the same input every call (smearing in place smooths it)
-            lq.stout_smear(g, 0.1, 3, (0, 1, 2, 3))
-        res["forward_ms"] = _events(torch, fwd, args.steps, args.warmup)
-        res["forward_ms_note"] = "3 steps from the thin links, including a links-sized device copy per call"
+        res["forward_ms"] = _events(torch, lambda: lq.stout_smear(g, 0.1, 3, (0, 1, 2, 3)), args.steps,
+                                    args.warmup, reset=lambda: g.tensor.copy_(f.tensor))
+        res["forward_ms_note"] = "3 steps from the thin links (restored before every call, untimed)"
         lq.stout_backward(f, rho, n, (0, 1, 2, 3), F, beta=6.0)
         forces[name] = F.download()
         if name == "f64" and getattr(args, "fd_links", 4) > 0:
@@ -366,7 +386,10 @@ def ape48(args, torch, lq, fieldgen):
     p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
     for name, prec in (("f32", lq.LQ_F32), ("f64", lq.LQ_F64)):
         f, _ = _field(lq, fieldgen, dims, 2, prec)
-        t = _events(torch, lambda: lq.ape_smear(f, alpha, n, (0, 1, 2, 3)), args.steps, args.warmup)
+        orig = f.tensor.clone()
+        t = _events(torch, lambda: lq.ape_smear(f, alpha, n, (0, 1, 2, 3)), args.steps, args.warmup,
+                    reset=lambda: f.tensor.copy_(orig))
+        del orig
         f64_flops = APE_PROJECTION_FLOPS + (APE_MIX_FLOPS if prec == lq.LQ_F64 else 0)
         out[name] = {"ms": t, "value": links / (t * 1e-3),
                      "roofline": {"bound": "alu", "pipe": "fp64", "fp64_flops_per_link": f64_flops,
@@ -398,7 +421,10 @@ def hyp32(args, torch, lq, fieldgen):
     p64 = 2.0 * bench.FP64_FMA_PER_CLK * mhz * 1e6
     for name, prec in (("f32", lq.LQ_F32), ("f64", lq.LQ_F64)):
         f, _ = _field(lq, fieldgen, dims, 2, prec)
-        t = _events(torch, lambda: lq.hyp_smear(f, 0.75, 0.6, 0.3, n), args.steps, args.warmup)
+        orig = f.tensor.clone()
+        t = _events(torch, lambda: lq.hyp_smear(f, 0.75, 0.6, 0.3, n), args.steps, args.warmup,
+                    reset=lambda: f.tensor.copy_(orig))
+        del orig
         f64_site = HYP_PROJECTIONS_PER_SITE * APE_PROJECTION_FLOPS + (HYP_MIX_FLOPS_PER_SITE if prec == lq.LQ_F64
                                                                       else 0)
         ach = f64_site * V * n / (t * 1e-3)
@@ -456,8 +482,8 @@ def apeforce24(args, torch, lq, fieldgen):
                            "note": "checkpoint_every=1; flops of the forward recompute included; Newton "
                                    "refinements of square roots and reciprocals not counted"}
         g = lq.Field(f.geom, lq.LQ_LINKS, prec)
-        g.tensor.copy_(f.tensor)
-        res["forward_ms"] = _events(torch, lambda: lq.ape_smear(g, alpha, n, (0, 1, 2, 3)), args.steps, args.warmup)
+        res["forward_ms"] = _events(torch, lambda: lq.ape_smear(g, alpha, n, (0, 1, 2, 3)), args.steps, args.warmup,
+                                    reset=lambda: g.tensor.copy_(f.tensor))
         out[name] = res
         del f, F, g
         torch.cuda.empty_cache()
@@ -493,8 +519,8 @@ def hypforce24(args, torch, lq, fieldgen):
         f64_site = n * (HYPF_F64_FLOPS_PER_SITE + (HYPF_MIX_FLOPS_PER_SITE if prec == lq.LQ_F64 else 0))
         ach = f64_site * V / (t * 1e-3)
         g = lq.Field(f.geom, lq.LQ_LINKS, prec)
-        g.tensor.copy_(f.tensor)
-        tf = _events(torch, lambda: lq.hyp_smear(g, *w, n), args.steps, args.warmup)
+        tf = _events(torch, lambda: lq.hyp_smear(g, *w, n), args.steps, args.warmup,
+                     reset=lambda: g.tensor.copy_(f.tensor))
         out[name] = {"ms": t, "value": n * V * 4 / (t * 1e-3), "forward_ms": tf,
                      "roofline": {"bound": "alu", "pipe": "fp64", "fp64_flops_per_link": f64_site / (4 * n),
                                   "achieved": ach / 1e12, "peak": p64 / 1e12, "frac": ach / p64, "unit": "TFLOP/s",
@@ -512,8 +538,8 @@ def micro16(args, torch, lq, fieldgen):
     V = int(np.prod(dims))
     f, U = _field(lq, fieldgen, dims, 1, lq.LQ_F64)
     g = lq.Field(f.geom, lq.LQ_LINKS, lq.LQ_F64)
-    g.tensor.copy_(f.tensor)
-    t_smear = _events(torch, lambda: lq.stout_smear(g, 0.1, 10, (0, 1, 2)), args.steps, args.warmup)
+    t_smear = _events(torch, lambda: lq.stout_smear(g, 0.1, 10, (0, 1, 2)), args.steps, args.warmup,
+                      reset=lambda: g.tensor.copy_(f.tensor))
     p_tr = []
     for mu in range(4):
         p_tr += [("loadl", 0, 0, mu, 0, 0), ("loadl", 1, 0, mu, mu, +1), ("mul", 2, 0, 1)]
