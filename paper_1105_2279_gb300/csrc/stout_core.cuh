@@ -289,12 +289,14 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
   d0 -= tq;
   d1 -= tq;
   d2 -= tq;
+  // explicit FMAs: a sum of two products left to the compiler may be fused
+  // either way, and differently in different kernels
   const double n01 = cnorm2(o01), n02 = cnorm2(o02), n12 = cnorm2(o12);
-  const double c1 = 0.5 * (d0 * d0 + d1 * d1 + d2 * d2) + n01 + n02 + n12;
+  const double c1 = fma(0.5, fma(d2, d2, fma(d1, d1, d0 * d0)), n01) + n02 + n12;
   // det Q = d0 d1 d2 - d0|o12|^2 - d1|o02|^2 - d2|o01|^2 + 2 Re(o01 o12 conj(o02))
   const cx<double> p = cmul(o01, o12);
-  const double re3 = p.re * o02.re + p.im * o02.im;
-  const double c0 = d0 * d1 * d2 - d0 * n12 - d1 * n02 - d2 * n01 + 2.0 * re3;
+  const double re3 = fma(p.re, o02.re, p.im * o02.im);
+  const double c0 = fma(2.0, re3, fma(-d2, n01, fma(-d1, n02, fma(-d0, n12, (d0 * d1) * d2))));
   if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {  // c1 >= +0: integer compare
     expiq_series<NR == 1 ? 7 : 9>(c0, c1, series_order<NR>(c1), f);
     return f;
@@ -327,7 +329,7 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
   double su, cu;
   sincos_red(u, &su, &cu);
   const cx<double> emiu = mkc(cu, -su);
-  const cx<double> e2iu = mkc(cu * cu - su * su, 2.0 * su * cu);
+  const cx<double> e2iu = mkc(fma(cu, cu, -su * su), 2.0 * su * cu);
   // h0 = (u^2 - w^2) e^{2iu} + e^{-iu} [8u^2 cos w + 2iu(3u^2 + w^2) xi0]
   const cx<double> h0 = cadd(cscale(e2iu, u2 - w2),
                              cmul(emiu, mkc(8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0)));
@@ -366,10 +368,10 @@ __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, d
   d1 -= tq;
   d2 -= tq;
   const double n01 = cnorm2(o01), n02 = cnorm2(o02), n12 = cnorm2(o12);
-  const double c1 = 0.5 * (d0 * d0 + d1 * d1 + d2 * d2) + n01 + n02 + n12;
+  const double c1 = fma(0.5, fma(d2, d2, fma(d1, d1, d0 * d0)), n01) + n02 + n12;   // as in ch_coefficients
   const cx<double> p = cmul(o01, o12);
-  const double re3 = p.re * o02.re + p.im * o02.im;
-  const double c0 = d0 * d1 * d2 - d0 * n12 - d1 * n02 - d2 * n01 + 2.0 * re3;
+  const double re3 = fma(p.re, o02.re, p.im * o02.im);
+  const double c0 = fma(2.0, re3, fma(-d2, n01, fma(-d1, n02, fma(-d0, n12, (d0 * d1) * d2))));
   if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {
     // FP64 links: the order of the f_j's series (tol 1e-17) plus one, which
     // keeps b_ij Q^j at FP64 rounding.  FP32 links: the f_j's own order (tol
@@ -418,7 +420,7 @@ __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, d
   double su, cu;
   sincos_red(u, &su, &cu);
   const cx<double> emiu = mkc(cu, -su);
-  const cx<double> e2iu = mkc(cu * cu - su * su, 2.0 * su * cu);
+  const cx<double> e2iu = mkc(fma(cu, cu, -su * su), 2.0 * su * cu);
   const cx<double> I = mkc(0.0, 1.0);
   cx<double> h[3], r1[3], r2[3];
   h[0] = cadd(cscale(e2iu, u2 - w2), cmul(emiu, mkc(8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0)));
@@ -468,9 +470,9 @@ template <typename R>
 __device__ __forceinline__ M3<R> expiq_assemble(const QH<R>& q, const QH<R>& q2, cx<R> f0, cx<R> f1,
                                                 cx<R> f2) {
   M3<R> e;
-  e.e[0] = cadd(f0, mkc(f1.re * q.d0 + f2.re * q2.d0, f1.im * q.d0 + f2.im * q2.d0));
-  e.e[4] = cadd(f0, mkc(f1.re * q.d1 + f2.re * q2.d1, f1.im * q.d1 + f2.im * q2.d1));
-  e.e[8] = cadd(f0, mkc(f1.re * q.d2 + f2.re * q2.d2, f1.im * q.d2 + f2.im * q2.d2));
+  e.e[0] = cadd(f0, mkc(fmaR(f2.re, q2.d0, f1.re * q.d0), fmaR(f2.im, q2.d0, f1.im * q.d0)));
+  e.e[4] = cadd(f0, mkc(fmaR(f2.re, q2.d1, f1.re * q.d1), fmaR(f2.im, q2.d1, f1.im * q.d1)));
+  e.e[8] = cadd(f0, mkc(fmaR(f2.re, q2.d2, f1.re * q.d2), fmaR(f2.im, q2.d2, f1.im * q.d2)));
   e.e[1] = cfma(f2, q2.o01, cmul(f1, q.o01));
   e.e[2] = cfma(f2, q2.o02, cmul(f1, q.o02));
   e.e[5] = cfma(f2, q2.o12, cmul(f1, q.o12));
