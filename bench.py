@@ -51,7 +51,8 @@ MATRIX_FLOPS_PER_LINK = 3019.0
 # FP32 cross products and the correction of row 2 96).
 REPROJECT_FLOPS_PER_LINK = 94.0
 REPROJECT_FP32_FLOPS_PER_LINK = 158.0
-# Cayley-Hamilton coefficients: c0 = det Q and c1 = tr(Q^2)/2 (35 flops), then
+# Cayley-Hamilton coefficients: c0 = det Q and c1 = tr(Q^2)/2 of Q made
+# traceless by d2 = -(d0 + d1) (1 + 9 for the |Q_jk|^2 + 6 + 19 = 35 flops), then
 # either the closed form (179 more) or the reduced Taylor series of degree
 # 2K+1 by Horner's rule (14 per pair of terms: 14 (K-1) + 7).  K depends on
 # c1, so the average is counted on the workload itself (lq.stout_ch_stats).

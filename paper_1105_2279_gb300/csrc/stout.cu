@@ -710,7 +710,11 @@ __global__ void k_expiq(const typename vec2<R>::type* __restrict__ Q, typename v
   q.o01 = m.e[1];
   q.o02 = m.e[2];
   q.o12 = m.e[5];
-  const CHCoef f = ch_coefficients<sizeof(R) == 4 ? 1 : 2>(to_f64(q.d0), to_f64(q.d1), to_f64(q.d2),
+  // any input: its trace removed in FP64 before the coefficients (which take
+  // the diagonal as traceless up to rounding)
+  const double d0 = to_f64(q.d0), d1 = to_f64(q.d1), d2 = to_f64(q.d2);
+  const double tq = (d0 + d1 + d2) * (1.0 / 3.0);
+  const CHCoef f = ch_coefficients<sizeof(R) == 4 ? 1 : 2>(d0 - tq, d1 - tq, d2 - tq,
                                                            mkc(to_f64(q.o01.re), to_f64(q.o01.im)),
                                                            mkc(to_f64(q.o02.re), to_f64(q.o02.im)),
                                                            mkc(to_f64(q.o12.re), to_f64(q.o12.im)));

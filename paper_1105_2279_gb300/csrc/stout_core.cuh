@@ -272,9 +272,30 @@ __device__ __forceinline__ void expiq_series_deriv(double c0, double c1, int K, 
   b2[2] = z0;
 }
 
+// c1 = tr(Q^2)/2 and c0 = det Q of the Hermitian Q with diagonal (d0, d1, d2)
+// and upper off-diagonal entries o01, o02, o12.  Q is traceless up to the
+// rounding of its diagonal; taking d2 = -(d0 + d1) makes it exactly traceless
+// in FP64 (the sum of two FP32 entries is exact, that of two FP64 entries
+// rounds once), so only d0 and d1 enter:
+//   c1 = d0 (d0 + d1) + d1^2 + |o01|^2 + |o02|^2 + |o12|^2
+//   c0 = -d0 d1 (d0 + d1) - d0 |o12|^2 - d1 |o02|^2 + (d0 + d1) |o01|^2 + 2 Re(o01 o12 conj(o02))
+// (35 flops).  The FMAs are explicit: a sum of two products left to the
+// compiler may be fused either way, and differently in different kernels.
+__device__ __forceinline__ void ch_invariants(double d0, double d1, cx<double> o01, cx<double> o02, cx<double> o12,
+                                              double& c0, double& c1) {
+  const double s01 = d0 + d1;   // -d2
+  const double n01 = cnorm2(o01), n02 = cnorm2(o02), n12 = cnorm2(o12);
+  c1 = fma(d0, s01, fma(d1, d1, n01)) + n02 + n12;
+  const cx<double> p = cmul(o01, o12);
+  const double re3 = fma(p.re, o02.re, p.im * o02.im);
+  c0 = fma(2.0, re3, fma(s01, n01, fma(-d1, n02, fma(-d0, n12, -(d0 * d1) * s01))));
+}
+
 // Cayley-Hamilton coefficients of exp(iQ) = f0 + f1 Q + f2 Q^2, in FP64
-// (Morningstar & Peardon 2004, Sec. III).  The input Q is re-made exactly
-// traceless in FP64 first.  For c1 <= 3/4 (all |lambda| <= 1, every link of
+// (Morningstar & Peardon 2004, Sec. III).  Q must be traceless up to
+// rounding (the stout step's Q is; lq_expiq removes the trace of its input
+// first) and is made exactly traceless in FP64 by taking d2 = -(d0 + d1)
+// (ch_invariants).  For c1 <= 3/4 (all |lambda| <= 1, every link of
 // a smearing run on fields with plaquette >~ 0.5) the reduced Taylor series
 // above; otherwise the paper's closed form, its quantities formed with few
 // FP64 instructions (fp64_math.cuh):
@@ -285,18 +306,9 @@ template <int NR = 2>
 __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d2, cx<double> o01,
                                                   cx<double> o02, cx<double> o12) {
   CHCoef f;
-  const double tq = (d0 + d1 + d2) * (1.0 / 3.0);
-  d0 -= tq;
-  d1 -= tq;
-  d2 -= tq;
-  // explicit FMAs: a sum of two products left to the compiler may be fused
-  // either way, and differently in different kernels
-  const double n01 = cnorm2(o01), n02 = cnorm2(o02), n12 = cnorm2(o12);
-  const double c1 = fma(0.5, fma(d2, d2, fma(d1, d1, d0 * d0)), n01) + n02 + n12;
-  // det Q = d0 d1 d2 - d0|o12|^2 - d1|o02|^2 - d2|o01|^2 + 2 Re(o01 o12 conj(o02))
-  const cx<double> p = cmul(o01, o12);
-  const double re3 = fma(p.re, o02.re, p.im * o02.im);
-  const double c0 = fma(2.0, re3, fma(-d2, n01, fma(-d1, n02, fma(-d0, n12, (d0 * d1) * d2))));
+  double c0, c1;
+  ch_invariants(d0, d1, o01, o02, o12, c0, c1);
+  (void)d2;
   if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {  // c1 >= +0: integer compare
     expiq_series<NR == 1 ? 7 : 9>(c0, c1, series_order<NR>(c1), f);
     return f;
@@ -363,15 +375,9 @@ template <int NR = 2>
 __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, double d2, cx<double> o01,
                                                          cx<double> o02, cx<double> o12) {
   CHDeriv r;
-  const double tq = (d0 + d1 + d2) * (1.0 / 3.0);
-  d0 -= tq;
-  d1 -= tq;
-  d2 -= tq;
-  const double n01 = cnorm2(o01), n02 = cnorm2(o02), n12 = cnorm2(o12);
-  const double c1 = fma(0.5, fma(d2, d2, fma(d1, d1, d0 * d0)), n01) + n02 + n12;   // as in ch_coefficients
-  const cx<double> p = cmul(o01, o12);
-  const double re3 = fma(p.re, o02.re, p.im * o02.im);
-  const double c0 = fma(2.0, re3, fma(-d2, n01, fma(-d1, n02, fma(-d0, n12, (d0 * d1) * d2))));
+  double c0, c1;
+  ch_invariants(d0, d1, o01, o02, o12, c0, c1);
+  (void)d2;
   if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {
     // FP64 links: the order of the f_j's series (tol 1e-17) plus one, which
     // keeps b_ij Q^j at FP64 rounding.  FP32 links: the f_j's own order (tol
