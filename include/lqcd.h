@@ -346,6 +346,40 @@ lq_status lq_stout_backward(const lq_field* thin_links, double rho, int n_steps,
                             const lq_field* grad_seed, double beta, lq_field* force_out,
                             lq_field* grad_out, const lq_backward_opts* opts, void* stream);
 
+/* One step of the stout force recursion of lq_stout_backward ([MP]
+ * Sec. IV), on the sites [s_begin, s_end) of LINKS fields of one geometry
+ * and precision: for callers that hold one part of a lattice (a t-slab with
+ * a halo slice on each side, see lq_stout_step_range; [W] Sec. 8 names
+ * multi-GPU parallelisation as future work) and run the recursion step by
+ * step, exchanging halos in between.  With U^(j+1) = stout step of U^(j):
+ *   G' = the gradient at U^(j+1) of the link, from `source`:
+ *     LQ_BWD_SOURCE_WILSON: -(beta/3) (sum of the staples of u_next, all
+ *                           planes): the Wilson action of U^(j+1) = u_next;
+ *     LQ_BWD_SOURCE_GIVEN:  g_in (a seed dS/dU^(j+1));
+ *     LQ_BWD_SOURCE_GATHER: g_in (G_U(local) of step j+1) plus the six
+ *                           staple-insertion terms of k_next (K of step j+1)
+ *                           on u_next (= U^(j+1)), for smeared directions;
+ *   with k_out (a link stage, u_cur = U^(j)): g_out = G_U(local) and
+ *     k_out = K (the gradient w.r.t. the bare staple sum) of step j, for the
+ *     directions in dirs_mask; other directions get g_out = G' and k_out
+ *     untouched;
+ *   without k_out (the last step, u_cur = the thin links): g_out (optional)
+ *     = G', the gradient at the thin links, and force_out (optional) =
+ *     TA(G' u_cur^dag).
+ * Reads of u_next, k_next and u_cur reach at most one site away from the
+ * range in every direction; g_in and the outputs only the range itself.
+ * Sites outside the range are left as they were.  Outputs must not alias
+ * each other or an input.  rho finite >= 0, beta finite, 0 <= s_begin <=
+ * s_end <= volume.  Results equal those of lq_stout_backward (checkpoints
+ * kept every step) bit for bit.  Asynchronous. */
+#define LQ_BWD_SOURCE_WILSON 0
+#define LQ_BWD_SOURCE_GIVEN 1
+#define LQ_BWD_SOURCE_GATHER 2
+lq_status lq_stout_backward_step(const lq_field* u_next, const lq_field* k_next, const lq_field* g_in,
+                                 const lq_field* u_cur, lq_field* g_out, lq_field* k_out, lq_field* force_out,
+                                 int source, double rho, double beta, unsigned dirs_mask, long long s_begin,
+                                 long long s_end, void* stream);
+
 /* Smears n_cfg independent LINKS fields (any geometries, one precision) with
  * one persistent launch per step over a device work list of (config, tile)
  * items; with opts->use_graph the n-step sequence is a replayed CUDA graph.

@@ -279,6 +279,19 @@ def stout_step_range(inp, out, rho, s_begin, s_end, dirs=(0, 1, 2, 3), stream=No
                                         int(s_end), byref(o), _stream(stream)), "lq_stout_step_range")
 
 
+LQ_BWD_SOURCE_WILSON, LQ_BWD_SOURCE_GIVEN, LQ_BWD_SOURCE_GATHER = 0, 1, 2
+
+
+def stout_backward_step(u_cur, source, rho, s_begin, s_end, dirs=(0, 1, 2, 3), u_next=None, k_next=None,
+                        g_in=None, g_out=None, k_out=None, force_out=None, beta=6.0, stream=None):
+    """One step of the stout force recursion on the sites [s_begin, s_end) (lq_stout_backward_step)."""
+    def h(f):
+        return f.handle if f is not None else None
+    _check(L.load().lq_stout_backward_step(h(u_next), h(k_next), h(g_in), u_cur.handle, h(g_out), h(k_out),
+                                           h(force_out), int(source), float(rho), float(beta), dirs_mask(dirs),
+                                           int(s_begin), int(s_end), _stream(stream)), "lq_stout_backward_step")
+
+
 def stout_smear_noalloc(links, rho, n_steps, dirs=(0, 1, 2, 3), stream=None):
     """lq_stout_smear_noalloc: same result as stout_smear, no device allocation (fields up to 32 MiB)."""
     _check(L.load().lq_stout_smear_noalloc(links.handle, float(rho), int(n_steps), dirs_mask(dirs), _stream(stream)),

@@ -59,6 +59,8 @@ SIGNATURES = {
     "lq_wilson_action": (c_int, [_P, c_double, POINTER(c_double), _P]),
     "lq_stout_smear": (c_int, [_P, c_double, c_int, c_uint, POINTER(LqStoutOpts), _P]),
     "lq_stout_backward": (c_int, [_P, c_double, c_int, c_uint, _P, c_double, _P, _P, POINTER(LqBackwardOpts), _P]),
+    "lq_stout_backward_step": (c_int, [_P, _P, _P, _P, _P, _P, _P, c_int, c_double, c_double, c_uint, c_longlong,
+                                       c_longlong, _P]),
     "lq_ape_backward": (c_int, [_P, c_double, c_int, c_uint, _P, c_double, _P, _P, POINTER(LqBackwardOpts), _P]),
     "lq_hyp_backward": (c_int, [_P, c_double, c_double, c_double, c_int, _P, c_double, _P, _P,
                                 POINTER(LqBackwardOpts), _P]),

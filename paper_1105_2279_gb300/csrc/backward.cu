@@ -189,6 +189,7 @@ template <typename R> struct BwdArgs {
   V2<R>* Kout;         // K of step j (link stage)
   V2<R>* Fout;         // force TA(G U^dag) at the thin links (final, may be NULL)
   GeomArgs g;
+  int s_begin, s_end;  // the sites the kernel handles (the whole lattice: 0, V)
   R w0, w1;            // stout: rho; APE: 1 - alpha and the staple coefficient
   R mbeta3;            // Wilson seed: -beta / 3
   unsigned dirs;
@@ -201,8 +202,8 @@ template <typename R, int SRC, int DST>
 __global__ void __launch_bounds__(128) k_bwd_step(BwdArgs<R> p) {
   const GeomArgs& g = p.g;
   const long long V = g.V;
-  const long long sl = (long long)(blockIdx.x / 4) * blockDim.x + threadIdx.x;
-  if (sl >= V) return;
+  const long long sl = p.s_begin + (long long)(blockIdx.x / 4) * blockDim.x + threadIdx.x;
+  if (sl >= p.s_end) return;
   const int s = (int)sl;
   const int a = blockIdx.x % 4;
   const long long off = (long long)a * 9 * V + s;
@@ -240,7 +241,8 @@ __global__ void __launch_bounds__(128) k_bwd_step(BwdArgs<R> p) {
 
 template <typename R, int SRC, int DST>
 static lq_status launch_bwd_step(const BwdArgs<R>& p, cudaStream_t s) {
-  const unsigned grid = (unsigned)(((p.g.V + 127) / 128) * 4);
+  const unsigned grid = (unsigned)((((long long)p.s_end - p.s_begin + 127) / 128) * 4);
+  if (grid == 0) return LQ_OK;
   k_bwd_step<R, SRC, DST><<<grid, 128, 0, s>>>(p);
   return launch_check("k_bwd_step");
 }
@@ -419,6 +421,8 @@ static lq_status backward_impl(const SmearArgs& sa, const lq_field* thin, int n,
   for (int mu = 0; mu < 4; ++mu) nd += (dirs >> mu) & 1u;
   BwdArgs<R> p{};
   p.g = g;
+  p.s_begin = 0;
+  p.s_end = (int)V;
   p.dirs = dirs;
   p.mbeta3 = (R)(-beta / 3.0);
   if (kind == Smearing::kStout) {
@@ -557,4 +561,83 @@ extern "C" lq_status lq_hyp_backward(const lq_field* thin, double a1, double a2,
   if (thin->prec == LQ_F64)
     return backward_impl<double>(sa, thin, n_steps, 15u, grad_seed, beta, force_out, grad_out, every, s);
   return backward_impl<float>(sa, thin, n_steps, 15u, grad_seed, beta, force_out, grad_out, every, s);
+}
+
+// One step of the stout force recursion on a site range (the building block
+// of lq_stout_backward for callers that hold one part of a lattice).
+template <typename R>
+static lq_status backward_step_range(const lq_field* u_next, const lq_field* k_next, const lq_field* g_in,
+                                     const lq_field* u_cur, lq_field* g_out, lq_field* k_out, lq_field* force_out,
+                                     int source, double rho, double beta, unsigned dirs, long long s_begin,
+                                     long long s_end, cudaStream_t s) {
+  BwdArgs<R> p{};
+  p.g = geom_args(u_cur->geom);
+  p.s_begin = (int)s_begin;
+  p.s_end = (int)s_end;
+  p.dirs = dirs;
+  p.w0 = (R)rho;
+  p.mbeta3 = (R)(-beta / 3.0);
+  p.Unext = u_next ? (const V2<R>*)u_next->ptr : nullptr;
+  p.Knext = k_next ? (const V2<R>*)k_next->ptr : nullptr;
+  p.Gin = g_in ? (const V2<R>*)g_in->ptr : nullptr;
+  p.Ucur = (const V2<R>*)u_cur->ptr;
+  p.Gout = g_out ? (V2<R>*)g_out->ptr : nullptr;
+  p.Kout = k_out ? (V2<R>*)k_out->ptr : nullptr;
+  p.Fout = force_out ? (V2<R>*)force_out->ptr : nullptr;
+  const int src = source == LQ_BWD_SOURCE_WILSON ? kSrcWilson : (source == LQ_BWD_SOURCE_GIVEN ? kSrcLoad : kSrcGather);
+  if (k_out) return launch_bwd_src<R, kDstStout>(src, p, s);
+  return launch_bwd_src<R, kDstFinal>(src, p, s);
+}
+
+extern "C" lq_status lq_stout_backward_step(const lq_field* u_next, const lq_field* k_next, const lq_field* g_in,
+                                            const lq_field* u_cur, lq_field* g_out, lq_field* k_out,
+                                            lq_field* force_out, int source, double rho, double beta,
+                                            unsigned dirs_mask, long long s_begin, long long s_end, void* stream) {
+  clear_error();
+  const char* who = "lq_stout_backward_step";
+  lq_status st = check_links(u_cur, who);
+  if (st != LQ_OK) return st;
+  if ((st = check_dirs(dirs_mask, who)) != LQ_OK) return st;
+  if (source != LQ_BWD_SOURCE_WILSON && source != LQ_BWD_SOURCE_GIVEN && source != LQ_BWD_SOURCE_GATHER) {
+    set_error("%s: source must be LQ_BWD_SOURCE_WILSON, _GIVEN or _GATHER", who);
+    return LQ_ERR_ARG;
+  }
+  const bool need_u_next = source != LQ_BWD_SOURCE_GIVEN, need_k_next = source == LQ_BWD_SOURCE_GATHER,
+             need_g_in = source != LQ_BWD_SOURCE_WILSON;
+  if ((need_u_next && !u_next) || (need_k_next && !k_next) || (need_g_in && !g_in)) {
+    set_error("%s: the source needs u_next (Wilson, gather), k_next (gather) and g_in (given, gather)", who);
+    return LQ_ERR_ARG;
+  }
+  if (k_out ? (!g_out || force_out) : (!g_out && !force_out)) {
+    set_error("%s: give g_out and k_out (a link stage), or g_out and/or force_out without k_out (the last step)",
+              who);
+    return LQ_ERR_ARG;
+  }
+  const lq_field* all[7] = {u_next, k_next, g_in, u_cur, g_out, k_out, force_out};
+  for (const lq_field* f : all) {
+    if (!f) continue;
+    if (f->kind != LQ_LINKS || f->prec != u_cur->prec || !same_geom(f->geom, u_cur->geom)) {
+      set_error("%s: every field must be LINKS of u_cur's geometry and precision", who);
+      return LQ_ERR_GEOM;
+    }
+  }
+  for (int i = 4; i < 7; ++i) {   // the outputs against every other argument
+    if (!all[i]) continue;
+    for (int k = 0; k < 7; ++k)
+      if (k != i && all[k] && all[k]->ptr == all[i]->ptr) {
+        set_error("%s: outputs must not alias each other or an input", who);
+        return LQ_ERR_ARG;
+      }
+  }
+  if (!(rho >= 0.0) || rho > 1e6 || !(beta == beta) || s_begin < 0 || s_end < s_begin ||
+      s_end > u_cur->geom.volume) {
+    set_error("%s: need finite rho >= 0, finite beta and 0 <= s_begin <= s_end <= volume", who);
+    return LQ_ERR_ARG;
+  }
+  cudaStream_t s = as_stream(stream);
+  if (u_cur->prec == LQ_F64)
+    return backward_step_range<double>(u_next, k_next, g_in, u_cur, g_out, k_out, force_out, source, rho, beta,
+                                       dirs_mask, s_begin, s_end, s);
+  return backward_step_range<float>(u_next, k_next, g_in, u_cur, g_out, k_out, force_out, source, rho, beta,
+                                    dirs_mask, s_begin, s_end, s);
 }

@@ -23,7 +23,8 @@ tensors with an NCCL group, host copies with a gloo group.  A single rank
 """
 import numpy as np
 
-from . import Field, Geometry, LQ_LINKS, plaquette_sums, stout_step_range
+from . import (Field, Geometry, LQ_BWD_SOURCE_GATHER, LQ_BWD_SOURCE_GIVEN, LQ_BWD_SOURCE_WILSON, LQ_LINKS,
+               plaquette_sums, stout_backward_step, stout_step_range)
 
 
 class TSlab:
@@ -115,6 +116,51 @@ def stout_smear(field, slab, rho, n_steps, dirs=(0, 1, 2, 3), group=None, stream
         cur, nxt = nxt, cur
     if n_steps % 2 == 1:
         field.tensor.copy_(work.tensor)
+
+
+def stout_backward(field, slab, rho, n_steps, dirs=(0, 1, 2, 3), force_out=None, grad_out=None, grad_seed=None,
+                   beta=6.0, group=None, stream=None):
+    """Gradient of S(stout^n(U)) w.r.t. the thin links of the lattice held
+    slab-wise by the ranks of `group`, as lq_stout_backward computes it for
+    the whole lattice (MP Sec. IV): S is the Wilson action of the smeared
+    field at `beta`, or given by its gradient `grad_seed` at U^(n) (this
+    rank's local field; owned slices read).  `field` holds this rank's thin
+    links (halos included) and is not modified; force_out and grad_out
+    (local LINKS fields) receive the force TA(G U^dag) and the gradient G on
+    the owned slices.  Collective: every rank of the group calls it.
+
+    The forward steps are kept (one local field per step, each with its
+    halos exchanged).  Each backward step reads K of the step after it one
+    slice beyond the owned ones, so K's halos are exchanged between the
+    steps, just as the links' are between forward steps; G passes between
+    steps at the link itself and needs no exchange."""
+    if force_out is None and grad_out is None:
+        raise ValueError("give force_out and/or grad_out")
+    s0, s1 = slab.interior
+    U = [Field(field.geom, LQ_LINKS, field.prec)]
+    U[0].tensor.copy_(field.tensor)
+    slab.exchange(U[0], group)
+    for _ in range(n_steps):
+        nxt = Field(field.geom, LQ_LINKS, field.prec)
+        nxt.tensor.copy_(U[-1].tensor)   # directions outside dirs pass through
+        stout_step_range(U[-1], nxt, rho, s0, s1, dirs, stream=stream)
+        slab.exchange(nxt, group)
+        U.append(nxt)
+    G = [Field(field.geom, LQ_LINKS, field.prec) for _ in range(2)]
+    K = [Field(field.geom, LQ_LINKS, field.prec) for _ in range(2)]
+    for f in K:
+        f.tensor.zero_()
+    source = LQ_BWD_SOURCE_GIVEN if grad_seed is not None else LQ_BWD_SOURCE_WILSON
+    g_in, k_next = grad_seed, None
+    for j in range(n_steps - 1, -1, -1):
+        g_out, k_out = G[j % 2], K[j % 2]
+        stout_backward_step(U[j], source, rho, s0, s1, dirs, u_next=U[j + 1], k_next=k_next, g_in=g_in,
+                            g_out=g_out, k_out=k_out, beta=beta, stream=stream)
+        slab.exchange(k_out, group)
+        source, g_in, k_next = LQ_BWD_SOURCE_GATHER, g_out, k_out
+    # the gather of step 0's K on the thin links (n = 0: the seed at them)
+    stout_backward_step(U[0], source, rho, s0, s1, dirs, u_next=U[0], k_next=k_next, g_in=g_in, g_out=grad_out,
+                        force_out=force_out, beta=beta, stream=stream)
 
 
 def plaquette(field, slab, group=None, stream=None):

@@ -74,3 +74,28 @@ def gpu_rank(rank, world, port, U, prec_name, rho, n, dirs, out):
     plaq = domain.plaquette(f, slab)
     out[rank] = (np.ascontiguousarray(slab.owned(f.download())), plaq)
     dist.destroy_process_group()
+
+
+def gpu_backward_rank(rank, world, port, U, seed, prec_name, rho, n, dirs, out):
+    """One rank of the t-split stout force on cuda:0 (host-staged gloo halo
+    exchanges between the steps): paper_1105_2279_gb300.domain.stout_backward."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1105_2279_gb300 as lq
+    from paper_1105_2279_gb300 import domain
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    prec = lq.LQ_F64 if prec_name == "f64" else lq.LQ_F32
+    lt, lz, ly, lx = U.shape[:4]
+    slab = domain.TSlab((lx, ly, lz, lt), rank, world)
+    g = slab.local_geometry()
+    f = lq.Field.from_host(g, lq.LQ_LINKS, prec, slab.local_from_global(U))
+    s = lq.Field.from_host(g, lq.LQ_LINKS, prec, slab.local_from_global(seed)) if seed is not None else None
+    F, G = lq.Field(g, lq.LQ_LINKS, prec), lq.Field(g, lq.LQ_LINKS, prec)
+    domain.stout_backward(f, slab, rho, n, dirs, force_out=F, grad_out=G, grad_seed=s, beta=6.0)
+    out[rank] = (np.ascontiguousarray(slab.owned(F.download())), np.ascontiguousarray(slab.owned(G.download())))
+    dist.destroy_process_group()

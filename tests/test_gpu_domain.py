@@ -93,3 +93,74 @@ def test_step_range_leaves_other_sites_untouched(gpu):
         lq.stout_step_range(a, out, 0.1, 3 * v3, 2 * v3, (0, 2))
     with pytest.raises(lq.LqError):
         lq.stout_step_range(a, a, 0.1, 0, v3, (0, 2))
+
+
+def _whole_force(U, prec, n, dirs, seed=None):
+    f = upload_links(U, prec)
+    F = lq.Field(f.geom, lq.LQ_LINKS, prec)
+    G = lq.Field(f.geom, lq.LQ_LINKS, prec)
+    s = upload_links(seed, prec) if seed is not None else None
+    lq.stout_backward(f, 0.1, n, dirs, F, grad_seed=s, beta=6.0, grad_out=G)
+    return F.download(), G.download()
+
+
+@pytest.mark.parametrize("prec,n,dirs,with_seed", [(lq.LQ_F64, 2, (0, 1, 2, 3), False),
+                                                   (lq.LQ_F32, 3, (0, 1, 2, 3), True),
+                                                   (lq.LQ_F64, 0, (0, 1, 2, 3), False)])
+def test_single_rank_force_equals_whole_lattice(gpu, prec, n, dirs, with_seed):
+    """domain.stout_backward on one rank (halos from its own edge slices) runs
+    the kernels of lq_stout_backward step by step over the owned sites:
+    force and gradient equal the whole lattice's bit for bit."""
+    dims = (6, 4, 6, 8)
+    U = fieldgen.near_identity_su3(dims, 713)
+    seed = fieldgen.haar_su3(dims, 714) * 0.5 if with_seed else None
+    F_ref, G_ref = _whole_force(U, prec, n, dirs, seed)
+    slab = domain.TSlab(dims, 0, 1)
+    g = slab.local_geometry()
+    f = lq.Field.from_host(g, lq.LQ_LINKS, prec, slab.local_from_global(U))
+    s = lq.Field.from_host(g, lq.LQ_LINKS, prec, slab.local_from_global(seed)) if with_seed else None
+    F, G = lq.Field(g, lq.LQ_LINKS, prec), lq.Field(g, lq.LQ_LINKS, prec)
+    domain.stout_backward(f, slab, 0.1, n, dirs, force_out=F, grad_out=G, grad_seed=s)
+    assert np.array_equal(slab.owned(F.download()), F_ref)
+    assert np.array_equal(slab.owned(G.download()), G_ref)
+
+
+@pytest.mark.parametrize("prec_name,n,dirs,with_seed", [("f64", 2, (0, 1, 2, 3), False),
+                                                        ("f32", 3, (0, 1, 2, 3), True),
+                                                        ("f32", 2, (0, 1, 2), False)])
+def test_two_ranks_force_equals_whole_lattice(gpu, prec_name, n, dirs, with_seed):
+    """The stout force of a lattice split into two t-slabs (two processes on
+    the one GPU, K's and the links' halos exchanged over gloo between the
+    steps) equals lq_stout_backward of the whole lattice bit for bit."""
+    dims = (8, 8, 8, 16)
+    prec = lq.LQ_F64 if prec_name == "f64" else lq.LQ_F32
+    U = fieldgen.near_identity_su3(dims, 715)
+    seed = fieldgen.haar_su3(dims, 716) * 0.5 if with_seed else None
+    F_ref, G_ref = _whole_force(U, prec, n, dirs, seed)
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    port = _free_port()
+    procs = [ctx.Process(target=dd_workers.gpu_backward_rank,
+                         args=(r, 2, port, U, seed, prec_name, 0.1, n, dirs, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    assert np.array_equal(np.concatenate([out[0][0], out[1][0]], axis=0), F_ref)
+    assert np.array_equal(np.concatenate([out[0][1], out[1][1]], axis=0), G_ref)
+
+
+def test_backward_step_checks_its_arguments(gpu):
+    dims = (4, 4, 4, 4)
+    f = upload_links(fieldgen.unit_links(dims), lq.LQ_F64)
+    g = lq.Field(f.geom, lq.LQ_LINKS, lq.LQ_F64)
+    k = lq.Field(f.geom, lq.LQ_LINKS, lq.LQ_F64)
+    with pytest.raises(lq.LqError, match="source needs"):          # gather without K of the next step
+        lq.stout_backward_step(f, lq.LQ_BWD_SOURCE_GATHER, 0.1, 0, 256, u_next=f, g_in=g, g_out=g, k_out=k)
+    with pytest.raises(lq.LqError, match="alias"):
+        lq.stout_backward_step(f, lq.LQ_BWD_SOURCE_WILSON, 0.1, 0, 256, u_next=f, g_out=f, k_out=k)
+    with pytest.raises(lq.LqError, match="s_begin"):
+        lq.stout_backward_step(f, lq.LQ_BWD_SOURCE_WILSON, 0.1, 0, 257, u_next=f, g_out=g, k_out=k)
+    with pytest.raises(lq.LqError, match="k_out"):                 # a link stage needs both outputs
+        lq.stout_backward_step(f, lq.LQ_BWD_SOURCE_WILSON, 0.1, 0, 256, u_next=f, k_out=k)
