@@ -74,7 +74,7 @@ FP32_FMA_PER_CLK = 152 * 128
 # 8,388,608 link updates, times the 42,467,328 link updates of one 48^3x96 launch
 # (traffic grows in proportion to the links); see profiles/.
 TRAFFIC_BYTES_PER_LINK_F32 = (632874240 + 581486592) / 8388608.0
-TRAFFIC_BYTES_PER_LINK_F64 = (2019492000 + 1226847000) / 8388608.0
+TRAFFIC_BYTES_PER_LINK_F64 = (2151617000 + 1189766000) / 8388608.0
 
 
 # The two-link product variant (3) forms each U_mu(y) U_nu(y+mu) once: 9 staple
