@@ -229,3 +229,42 @@ def test_jacobi_launch_shape_checked_before_device_work(lqlib):
     o = LqJacobiOpts(4, 0, 0, 0)       # struct_size below the first option
     assert lib.lq_jacobi_smear_ex(U, v, 0.1, 1, 1.0, 15, ctypes.byref(o), None) == -1
     assert lib.lq_field_free(U) == 0 and lib.lq_field_free(v) == 0
+
+
+def test_backward_step_arguments_checked_before_device_work(lqlib):
+    """lq_stout_backward_step refuses, before any CUDA call (the fields point
+    at unmapped addresses), a gather without K of the next step, a link stage
+    without both outputs, an output that aliases an input, a site range past
+    the volume, an unknown source and fields of another geometry."""
+    lib = lqlib.capi()
+    g = lqlib.Geometry((2, 2, 2, 2))
+    g2 = lqlib.Geometry((2, 2, 2, 4))
+
+    def wrap(geom, addr):
+        h = ctypes.c_void_p()
+        nb = lqlib.field_bytes(geom, lqlib.LQ_LINKS, lqlib.LQ_F64)
+        assert lib.lq_field_wrap(geom.handle, lqlib.LQ_LINKS, lqlib.LQ_F64, ctypes.c_void_p(addr), nb,
+                                 ctypes.byref(h)) == 0
+        return h
+    u, kn, gi, go, ko, other = (wrap(g, 0x100000 * (i + 1)) for i in range(6))
+    far = wrap(g2, 0x1000000)
+    V = 16
+    W, GIVEN, GATHER = lqlib.LQ_BWD_SOURCE_WILSON, lqlib.LQ_BWD_SOURCE_GIVEN, lqlib.LQ_BWD_SOURCE_GATHER
+    cases = [
+        ((u, None, gi, u, go, ko, None, GATHER, 0, V), b"source needs"),
+        ((None, None, None, u, go, ko, None, GIVEN, 0, V), b"source needs"),
+        ((u, None, None, u, None, ko, None, W, 0, V), b"k_out"),
+        ((u, None, None, u, go, ko, other, W, 0, V), b"k_out"),
+        ((u, None, None, u, u, ko, None, W, 0, V), b"alias"),
+        ((u, None, None, u, go, go, None, W, 0, V), b"alias"),
+        ((u, None, None, u, go, ko, None, W, 0, V + 1), b"s_begin"),
+        ((u, None, None, u, go, ko, None, W, 5, 4), b"s_begin"),
+        ((u, None, None, u, go, ko, None, 7, 0, V), b"source must"),
+        ((far, None, None, u, go, ko, None, W, 0, V), b"geometry"),
+    ]
+    for (un, kk, gg, uc, g_o, k_o, f_o, src, s0, s1), msg in cases:
+        st = lib.lq_stout_backward_step(un, kk, gg, uc, g_o, k_o, f_o, src, 0.1, 6.0, 15, s0, s1, None)
+        assert st < 0, msg
+        assert msg in lib.lq_last_error(), (msg, lib.lq_last_error())
+    for h in (u, kn, gi, go, ko, other, far):
+        assert lib.lq_field_free(h) == 0
