@@ -2,13 +2,15 @@
 // transfers pipelined against the smearing.  The lattice is cut into slabs of
 // whole t-slices (contiguous site ranges in the lexicographic order, so a slab
 // is one contiguous piece of the host AoS array and of every SoA plane).
-//   upload stream:   per slab, H2D copy into an AoS staging buffer, then the
-//                    AoS -> SoA transpose of that slab; event up[i].
+//   upload streams:  per slab, H2D copy into an AoS staging buffer, then (on
+//                    a second stream) the AoS -> SoA transpose of that slab;
+//                    event up[i].
 //   compute stream:  step 1 of slab i waits for up[i-1], up[i], up[i+1] (the
 //                    staples reach one t-slice into each neighbour); after
 //                    the last step of slab i, event fin[i].
-//   download stream: per slab, waits for fin[i], transposes the slab back into
-//                    the staging buffer and copies it to the host.
+//   download streams: per slab, waits for fin[i], transposes the slab back
+//                    into the staging buffer and (on a second stream) copies
+//                    it to the host.
 // Step k of a slab reads field (k-1)%2 and writes field k%2, so (k, i) must
 // follow (k-1, j) for the slabs j next to i (their reads of field k%2 and
 // the values it reads).  The first two and the last two steps run as
@@ -32,13 +34,17 @@ using namespace lq;
 
 namespace {
 
+// Copies and transposes of a direction run on separate streams, so that the
+// transpose of one slab overlaps the host-link copy of the next (uploads) or
+// of the previous one (downloads): a slab's copy takes ~1 ms over the host
+// link, its transpose ~0.1 ms on the SMs.
 struct Streams {
-  cudaStream_t up = nullptr, down = nullptr;
+  cudaStream_t up = nullptr, down = nullptr, upx = nullptr, downx = nullptr;
   std::vector<cudaEvent_t> ev;
   ~Streams() {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
-    if (up) cudaStreamDestroy(up);
-    if (down) cudaStreamDestroy(down);
+    for (cudaStream_t q : {up, down, upx, downx})
+      if (q) cudaStreamDestroy(q);
   }
   // The transfer streams get the highest priority: their transposes are short
   // and must not queue behind the tens of thousands of pending blocks of a
@@ -50,6 +56,11 @@ struct Streams {
       st = cuda_check(cudaStreamCreateWithPriority(&up, cudaStreamNonBlocking, greatest), "upload stream");
     if (st == LQ_OK)
       st = cuda_check(cudaStreamCreateWithPriority(&down, cudaStreamNonBlocking, greatest), "download stream");
+    if (st == LQ_OK)
+      st = cuda_check(cudaStreamCreateWithPriority(&upx, cudaStreamNonBlocking, greatest), "upload transpose stream");
+    if (st == LQ_OK)
+      st = cuda_check(cudaStreamCreateWithPriority(&downx, cudaStreamNonBlocking, greatest),
+                      "download transpose stream");
     for (int i = 0; i < n_events && st == LQ_OK; ++i) {
       cudaEvent_t e;
       st = cuda_check(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "pipeline event");
@@ -188,10 +199,12 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
   }
 
   Streams ps;
-  if ((st = ps.make(2 * nc + 2)) != LQ_OK) return st;
-  cudaEvent_t* up = ps.ev.data();
-  cudaEvent_t* fin = ps.ev.data() + nc;
-  cudaEvent_t start = ps.ev[2 * nc], done = ps.ev[2 * nc + 1];
+  if ((st = ps.make(4 * nc + 2)) != LQ_OK) return st;
+  cudaEvent_t* up = ps.ev.data();            // slab i transposed in (and its pass-through copies)
+  cudaEvent_t* fin = ps.ev.data() + nc;      // slab i's last step done
+  cudaEvent_t* copied = ps.ev.data() + 2 * nc;   // slab i copied in
+  cudaEvent_t* out_ready = ps.ev.data() + 3 * nc;  // slab i transposed out
+  cudaEvent_t start = ps.ev[4 * nc], done = ps.ev[4 * nc + 1];
 
   void* f[2] = {nullptr, nullptr};
   void* stage = nullptr;
@@ -204,6 +217,8 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
   if (st == LQ_OK) st = cuda_check(cudaEventRecord(start, s), "pipeline start");
   if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(ps.up, start, 0), "pipeline start");
   if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(ps.down, start, 0), "pipeline start");
+  if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(ps.upx, start, 0), "pipeline start");
+  if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(ps.downx, start, 0), "pipeline start");
 
   const size_t site_bytes = 4 * 9 * eb;
   const size_t plane = (size_t)V * eb;
@@ -219,19 +234,21 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
                                     ps.up),
                     "lq_stout_smear_host upload");
     tr.close(t, ps.up);
-    t = tr.open("to_soa", i, 0, ps.up);
-    if (st == LQ_OK) st = transpose_range(stage, f[0], g, LQ_LINKS, prec, true, sb[i], sb[i + 1], ps.up);
-    tr.close(t, ps.up);
+    if (st == LQ_OK) st = cuda_check(cudaEventRecord(copied[i], ps.up), "pipeline copy event");
+    if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(ps.upx, copied[i], 0), "pipeline wait");
+    t = tr.open("to_soa", i, 0, ps.upx);
+    if (st == LQ_OK) st = transpose_range(stage, f[0], g, LQ_LINKS, prec, true, sb[i], sb[i + 1], ps.upx);
+    tr.close(t, ps.upx);
     // links outside dirs are never written: the work field needs them too
     for (int mu = 0; mu < 4 && st == LQ_OK && n_steps > 0; ++mu)
       if (!((dirs_mask >> mu) & 1u))
         for (int c = 0; c < 9 && st == LQ_OK; ++c) {
           const size_t po = (size_t)(mu * 9 + c) * plane + (size_t)sb[i] * eb;
           st = cuda_check(cudaMemcpyAsync((char*)f[1] + po, (const char*)f[0] + po, (size_t)(sb[i + 1] - sb[i]) * eb,
-                                          cudaMemcpyDeviceToDevice, ps.up),
+                                          cudaMemcpyDeviceToDevice, ps.upx),
                           "lq_stout_smear_host pass-through copy");
         }
-    if (st == LQ_OK) st = cuda_check(cudaEventRecord(up[i], ps.up), "pipeline upload event");
+    if (st == LQ_OK) st = cuda_check(cudaEventRecord(up[i], ps.upx), "pipeline upload event");
   }
 
   // (step, slab) items: the first two and the last two steps in wavefront
@@ -302,10 +319,12 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
   for (int i : done_order) {
     if (st != LQ_OK) break;
     const size_t off = (size_t)sb[i] * site_bytes, len = (size_t)(sb[i + 1] - sb[i]) * site_bytes;
-    st = cuda_check(cudaStreamWaitEvent(ps.down, fin[i], 0), "pipeline wait");
-    int t = tr.open("to_aos", i, n_steps, ps.down);
-    if (st == LQ_OK) st = transpose_range(result, stage, g, LQ_LINKS, prec, false, sb[i], sb[i + 1], ps.down);
-    tr.close(t, ps.down);
+    st = cuda_check(cudaStreamWaitEvent(ps.downx, fin[i], 0), "pipeline wait");
+    int t = tr.open("to_aos", i, n_steps, ps.downx);
+    if (st == LQ_OK) st = transpose_range(result, stage, g, LQ_LINKS, prec, false, sb[i], sb[i + 1], ps.downx);
+    tr.close(t, ps.downx);
+    if (st == LQ_OK) st = cuda_check(cudaEventRecord(out_ready[i], ps.downx), "pipeline transpose event");
+    if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(ps.down, out_ready[i], 0), "pipeline wait");
     t = tr.open("d2h", i, n_steps, ps.down);
     if (st == LQ_OK)
       st = cuda_check(cudaMemcpyAsync((char*)host_out + off, (const char*)stage + off, len, cudaMemcpyDeviceToHost,
@@ -330,8 +349,7 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
   lq_status st2 = cuda_check(cudaEventRecord(done, ps.down), "pipeline end");
   if (st2 == LQ_OK) st2 = cuda_check(cudaStreamWaitEvent(s, done, 0), "pipeline end");
   if (st != LQ_OK || st2 != LQ_OK) {
-    cudaStreamSynchronize(ps.up);
-    cudaStreamSynchronize(ps.down);
+    for (cudaStream_t q : {ps.up, ps.upx, ps.down, ps.downx}) cudaStreamSynchronize(q);
   }
   for (void* p : {f[0], f[1], stage})
     if (p) scratch_free(p, s);
