@@ -142,6 +142,8 @@ lq_status stout_choose(const lq_field* f, double rho, unsigned dirs, int reproje
 
 // Reductions shared by several entry points.
 lq_status plaquette_sums(const lq_field* links, double out_planes[2], cudaStream_t s);
+lq_status plaquette_sums_device(const lq_field* links, double* dev_totals, cudaStream_t s);
+void plaquette_from_sums(const double sums[2], long long volume, double out[3]);
 
 // Registered cleanup callbacks for lq_free_all.
 void register_cache_release(void (*fn)());

@@ -115,6 +115,36 @@ lq_status plaquette_sums(const lq_field* links, double out_planes[2], cudaStream
   return plaquette_sums_range(links, 0, links->geom.volume, out_planes, s);
 }
 
+// The two plane sums of the whole field into dev_totals[0..1] on the device,
+// stream-ordered on s (the same kernels and order as plaquette_sums, without
+// the read-back): a caller that reads them back on another stream.
+lq_status plaquette_sums_device(const lq_field* links, double* dev_totals, cudaStream_t s) {
+  const GeomArgs g = geom_args(links->geom);
+  const long long V = links->geom.volume;
+  const int grid = reduce_grid(V);
+  double* parts = nullptr;
+  lq_status st = scratch_alloc((void**)&parts, sizeof(double) * 2 * grid, s, "lq_plaquette");
+  if (st != LQ_OK) return st;
+  if (links->prec == LQ_F64)
+    k_plaquette<double><<<grid, kReduceThreads, 0, s>>>((const double2*)links->ptr, g, 0, V, parts);
+  else
+    k_plaquette<float><<<grid, kReduceThreads, 0, s>>>((const float2*)links->ptr, g, 0, V, parts);
+  st = launch_check("lq_plaquette");
+  if (st == LQ_OK) {
+    k_reduce_partials<2><<<1, kReduceThreads, 0, s>>>(parts, grid, dev_totals);
+    st = launch_check("lq_plaquette");
+  }
+  scratch_free(parts, s);
+  return st;
+}
+
+void plaquette_from_sums(const double sums[2], long long volume, double out[3]) {
+  const double V = (double)volume;
+  out[0] = (sums[0] + sums[1]) / (18.0 * V);
+  out[1] = sums[0] / (9.0 * V);
+  out[2] = sums[1] / (9.0 * V);
+}
+
 }  // namespace lq
 
 using namespace lq;
@@ -130,10 +160,7 @@ extern "C" lq_status lq_plaquette(const lq_field* links, double out[3], void* st
   double sums[2];
   st = plaquette_sums(links, sums, as_stream(stream));
   if (st != LQ_OK) return st;
-  const double V = (double)links->geom.volume;
-  out[0] = (sums[0] + sums[1]) / (18.0 * V);
-  out[1] = sums[0] / (9.0 * V);
-  out[2] = sums[1] / (9.0 * V);
+  plaquette_from_sums(sums, links->geom.volume, out);
   return LQ_OK;
 }
 

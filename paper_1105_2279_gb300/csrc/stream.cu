@@ -199,12 +199,12 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
   }
 
   Streams ps;
-  if ((st = ps.make(4 * nc + 2)) != LQ_OK) return st;
+  if ((st = ps.make(4 * nc + 3)) != LQ_OK) return st;
   cudaEvent_t* up = ps.ev.data();            // slab i transposed in (and its pass-through copies)
   cudaEvent_t* fin = ps.ev.data() + nc;      // slab i's last step done
   cudaEvent_t* copied = ps.ev.data() + 2 * nc;   // slab i copied in
   cudaEvent_t* out_ready = ps.ev.data() + 3 * nc;  // slab i transposed out
-  cudaEvent_t start = ps.ev[4 * nc], done = ps.ev[4 * nc + 1];
+  cudaEvent_t start = ps.ev[4 * nc], done = ps.ev[4 * nc + 1], plaq_ready = ps.ev[4 * nc + 2];
 
   void* f[2] = {nullptr, nullptr};
   void* stage = nullptr;
@@ -332,6 +332,11 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
                       "lq_stout_smear_host download");
     tr.close(t, ps.down);
   }
+  // the plaquette right after the last step; its two sums are read back on
+  // the download stream behind the slab copies (a read-back on s would wait
+  // for the copy engine all the same, and hold up the end of the call)
+  double* dev_sums = nullptr;
+  double sums[2] = {0.0, 0.0};
   if (st == LQ_OK && plaq_out) {
     lq_field tmp;
     tmp.geom = g;
@@ -340,9 +345,15 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
     tmp.ptr = result;
     tmp.bytes = bytes;
     tmp.owned = false;
+    st = scratch_alloc((void**)&dev_sums, 2 * sizeof(double), s, "lq_stout_smear_host plaquette");
     const int t = tr.open("plaq", -1, n_steps, s);
-    st = lq_plaquette(&tmp, plaq_out, stream);
+    if (st == LQ_OK) st = plaquette_sums_device(&tmp, dev_sums, s);
     tr.close(t, s);
+    if (st == LQ_OK) st = cuda_check(cudaEventRecord(plaq_ready, s), "pipeline plaquette event");
+    if (st == LQ_OK) st = cuda_check(cudaStreamWaitEvent(ps.down, plaq_ready, 0), "pipeline wait");
+    if (st == LQ_OK)
+      st = cuda_check(cudaMemcpyAsync(sums, dev_sums, sizeof(sums), cudaMemcpyDeviceToHost, ps.down),
+                      "lq_stout_smear_host plaquette read-back");
   }
   // the scratch goes back to the pool in s's order, after the downloads; on
   // an error the side streams may still hold work that s never waited for
@@ -351,9 +362,10 @@ extern "C" lq_status lq_stout_smear_host(const void* host_in, void* host_out, co
   if (st != LQ_OK || st2 != LQ_OK) {
     for (cudaStream_t q : {ps.up, ps.upx, ps.down, ps.downx}) cudaStreamSynchronize(q);
   }
-  for (void* p : {f[0], f[1], stage})
+  for (void* p : {f[0], f[1], stage, (void*)dev_sums})
     if (p) scratch_free(p, s);
   const lq_status st3 = cuda_check(cudaStreamSynchronize(s), "lq_stout_smear_host sync");
+  if (st == LQ_OK && st2 == LQ_OK && st3 == LQ_OK && plaq_out) plaquette_from_sums(sums, V, plaq_out);
   if (st == LQ_OK && st2 == LQ_OK && st3 == LQ_OK) tr.write();
   if (st != LQ_OK) return st;
   return st2 != LQ_OK ? st2 : st3;

@@ -81,13 +81,14 @@ def test_host_stream_rejects_bad_arguments(gpu):
         lq.stout_smear_host(h.reshape(-1)[:10], out, dims, lq.LQ_F64, 0.1, 1)  # wrong size (binding check)
 
 
-@pytest.mark.parametrize("n", [3, 6])
+@pytest.mark.parametrize("n", [3, 6, 7])
 def test_host_stream_trace_respects_dependencies(gpu, tmp_path, monkeypatch, n):
     """LQ_PIPELINE_TRACE timeline: every operation is recorded once, and on the
     device clock each step-1 launch starts after its slab's and both
     neighbours' transposes ended, each step after the previous step of the
     neighbouring slabs (or the previous whole-lattice launch: with more than
-    four steps, the middle steps run whole, slab -1), and each download after
+    four steps, the steps between the first two and the last two run whole,
+    slab -1), and each download after
     the slab's last step."""
     dims, nc = (4, 4, 4, 12), 6
     path = tmp_path / "trace.txt"
