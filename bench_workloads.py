@@ -207,9 +207,9 @@ def backward_fd(lq, fieldgen, thin, F, rho, n, beta, n_links, eps=1e-4, seed=44)
 # G_Omega 30, exp(iQ) 70, E^dag G' 198, G_Omega^dag C 216, K 216), the
 # factored six-term gather (3 directions x 2 groups x (2 products + 3
 # accumulating products) = 6264), and in FP64 the coefficients with their
-# derivatives: 35 + 48 + 24 per differentiated Horner step (2K + 2 steps for
-# the FP32 links' series order K, 2K + 4 for the FP64 links', read from
-# lq.stout_ch_stats of the links themselves).
+# derivatives: 35 + 48 + 24 per differentiated Horner step (2K + 4 steps for
+# the links' series order K plus one, K read from lq.stout_ch_stats of the
+# links themselves).
 BWD_LOCAL_FLOPS = 2484 + 216 + 20 + 40 + 198 + 148 + 684 + 30 + 70 + 198 + 216 + 216
 BWD_GATHER_FLOPS = 6264
 WILSON_GRAD_FLOPS = 2484 + 18
@@ -233,10 +233,10 @@ def backward24(args, torch, lq, fieldgen):
         stats64 = lq.stout_ch_stats(g64, rho, n, (0, 1, 2, 3))
         del g64
         mean_k = stats64[2] / max(1, stats64[1])
-        # the derivative series runs at the links' own table order (FP32 links) or
-        # that order plus one (FP64 links): 2K + 2 or 2K + 4 differentiated steps
+        # the derivative series runs at the links' own table order plus one:
+        # 2K + 4 differentiated steps
         own_k = stats[2] / max(1, stats[1])
-        ch_deriv = 35 + 48 + 24 * (2 * own_k + (4 if prec == lq.LQ_F64 else 2))
+        ch_deriv = 35 + 48 + 24 * (2 * own_k + 4)
         fwd_f64 = bench.ch_flops_per_link(stats) + (bench.REPROJECT_FLOPS_PER_LINK if prec == lq.LQ_F32
                                                      else bench.MATRIX_FLOPS_PER_LINK)
         algebra = n * (BWD_LOCAL_FLOPS + BWD_GATHER_FLOPS) + WILSON_GRAD_FLOPS + FORCE_FLOPS

@@ -159,26 +159,30 @@ constexpr long long dbl_bits(double x) {
 // Largest c1 handled by the series (|lambda| <= 1); above it the closed form.
 #define LQ_SERIES_C1_MAX 0.75
 
-// Series order for c1: thresholds (3/4)(tol (2K+2)!)^(1/(K+1)) for K = 1..;
-// tol = 1e-13 on FP32 links (the f_j are rounded to FP32), 1e-17 on FP64.
-template <int NR> __device__ __forceinline__ int series_order(double c1) {
+// Series order for c1: thresholds (3/4)(tol (2K+2)!)^(1/(K+1)) for K = 1..,
+// the c1 below which the first omitted term, |Q|^(2K+2)/(2K+2)! with
+// |Q|^2 <= 4 c1 / 3, stays below tol: tol = 1e-10 for the f_j of FP32 links
+// (they are rounded to FP32, 6e-8), 1e-17 on FP64 links.  The stout force
+// differentiates the series at one order more than the f_j's.
+__device__ __forceinline__ int series_order_f32(double c1) {
   const long long b = __double_as_longlong(c1);
-  if (NR == 1) {
-    constexpr long long t[6] = {dbl_bits(1.161895e-06), dbl_bits(0.000312012573), dbl_bits(0.00597642391),
-                                dbl_bits(0.0386379317), dbl_bits(0.142928035), dbl_bits(0.380920096)};
-    int K = 1;
+  constexpr long long t[5] = {dbl_bits(3.67423461e-05), dbl_bits(0.00312012573), dbl_bits(0.0336079014),
+                              dbl_bits(0.153820376), dbl_bits(0.451978133)};
+  int K = 1;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) K += (b > t[i]);
-    return K;   // <= 7: K = 7 covers c1 <= 0.8225
-  } else {
-    constexpr long long t[8] = {dbl_bits(1.161895e-08), dbl_bits(1.44823408e-05), dbl_bits(0.000597642391),
-                                dbl_bits(0.00612369949), dbl_bits(0.0307929118), dbl_bits(0.102189274),
-                                dbl_bits(0.260099018), dbl_bits(0.552627494)};
-    int K = 1;
+  for (int i = 0; i < 5; ++i) K += (b > t[i]);
+  return K;   // <= 6: K = 6 covers c1 <= 1.0219
+}
+
+__device__ __forceinline__ int series_order_f64(double c1) {
+  const long long b = __double_as_longlong(c1);
+  constexpr long long t[8] = {dbl_bits(1.161895e-08), dbl_bits(1.44823408e-05), dbl_bits(0.000597642391),
+                              dbl_bits(0.00612369949), dbl_bits(0.0307929118), dbl_bits(0.102189274),
+                              dbl_bits(0.260099018), dbl_bits(0.552627494)};
+  int K = 1;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) K += (b > t[i]);
-    return K;   // <= 9: K = 9 covers c1 <= 1.032
-  }
+  for (int i = 0; i < 8; ++i) K += (b > t[i]);
+  return K;   // <= 9: K = 9 covers c1 <= 1.032
 }
 
 // f0 + f1 Q + f2 Q^2 = sum_{n <= 2K+1} (iQ)^n / n!  (c1 <= LQ_SERIES_C1_MAX).
@@ -310,7 +314,7 @@ __device__ __forceinline__ CHCoef ch_coefficients(double d0, double d1, double d
   ch_invariants(d0, d1, o01, o02, o12, c0, c1);
   (void)d2;
   if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {  // c1 >= +0: integer compare
-    expiq_series<NR == 1 ? 7 : 9>(c0, c1, series_order<NR>(c1), f);
+    expiq_series<NR == 1 ? 6 : 9>(c0, c1, NR == 1 ? series_order_f32(c1) : series_order_f64(c1), f);
     return f;
   }
   f.k = 0;
@@ -379,13 +383,12 @@ __device__ __forceinline__ CHDeriv ch_coefficients_deriv(double d0, double d1, d
   ch_invariants(d0, d1, o01, o02, o12, c0, c1);
   (void)d2;
   if (__double_as_longlong(c1) <= dbl_bits(LQ_SERIES_C1_MAX)) {
-    // FP64 links: the order of the f_j's series (tol 1e-17) plus one, which
-    // keeps b_ij Q^j at FP64 rounding.  FP32 links: the f_j's own order (tol
-    // 1e-13); the truncated derivatives then enter d exp(iQ) = sum_j (b1_j dc1
-    // + b2_j dc0) Q^j + f_j dQ^j with an error <= 2.3e-10 |dQ| over the whole
-    // series domain (dc1 ~ 2|Q||dQ|, dc0 ~ 3|Q|^2 |dQ|), 250x below the FP32
-    // rounding of the links' gradient.
-    expiq_series_deriv<10>(c0, c1, NR == 1 ? series_order<1>(c1) : series_order<2>(c1) + 1, r.f, r.b1, r.b2);
+    // The order of the f_j's series plus one.  FP64 links: this keeps b_ij Q^j
+    // at FP64 rounding.  FP32 links: the truncated derivatives enter
+    // d exp(iQ) = sum_j (b1_j dc1 + b2_j dc0) Q^j + f_j dQ^j with an error
+    // <= 2.4e-12 |dQ| over the whole series domain (dc1 ~ 2|Q||dQ|,
+    // dc0 ~ 3|Q|^2 |dQ|), far below the FP32 rounding of the links' gradient.
+    expiq_series_deriv<10>(c0, c1, (NR == 1 ? series_order_f32(c1) : series_order_f64(c1)) + 1, r.f, r.b1, r.b2);
     return r;
   }
   if (!(c1 >= LQ_C1_SERIES)) {  // NaN (small c1 took the series)

@@ -141,16 +141,16 @@ def test_series_derivative_recurrence(c1, frac):
 
 
 def test_fp32_derivative_series_order_is_enough():
-    """FP32 links differentiate the series at the f_j's own order (FP32 table,
-    truncation bound 1e-13): over the whole series domain the truncated
+    """FP32 links differentiate the series at one order more than the f_j's
+    (FP32 table, tol 1e-10): over the whole series domain the truncated
     b1_j = df_j/dc1 and b2_j = df_j/dc0 enter d exp(iQ) = sum_j (b1_j dc1 +
-    b2_j dc0) Q^j + ... with an error <= 2.3e-10 per unit |dQ| (dc1 ~ 2|Q||dQ|,
+    b2_j dc0) Q^j + ... with an error <= 2.4e-12 per unit |dQ| (dc1 ~ 2|Q||dQ|,
     dc0 ~ 3|Q|^2 |dQ|), far below the FP32 rounding of the gradient (6e-8);
     checked against the series taken to order 12."""
-    th = [1.161895e-06, 0.000312012573, 0.00597642391, 0.0386379317, 0.142928035, 0.380920096]
+    th = [3.67423461e-05, 0.00312012573, 0.0336079014, 0.153820376, 0.451978133]
     worst = 0.0
     for c1 in np.geomspace(1e-12, 0.75, 300):
-        K = 1 + sum(c1 > t for t in th)
+        K = 2 + sum(c1 > t for t in th)
         q = np.sqrt(4.0 * c1 / 3.0)
         for frac in (-0.99, -0.5, 0.0, 0.5, 0.99):
             c0 = frac * 2.0 * (c1 / 3.0) ** 1.5
@@ -159,7 +159,31 @@ def test_fp32_derivative_series_order_is_enough():
             e1 = max(abs(b1[j] - B1[j]) * q ** j for j in range(3)) * 2.0 * q
             e2 = max(abs(b2[j] - B2[j]) * q ** j for j in range(3)) * 3.0 * q * q
             worst = max(worst, e1, e2)
-    assert worst <= 2.3e-10, worst
+    assert worst <= 2.4e-12, worst
+
+
+def test_fp32_forward_series_order_is_enough():
+    """The f_j of FP32 links come from the series at the order of the FP32
+    table (tol 1e-10: K = 1 + the number of thresholds below c1, at most 6):
+    over the whole series domain (c1 <= 3/4, every c0 of the cubic's range)
+    the truncated f_j, weighted by |Q|^j <= (4 c1 / 3)^(j/2), stay within
+    1e-10 of the series taken to order 14, 600x below the FP32 rounding of
+    the f_j; the thresholds are (3/4)(tol (2K+2)!)^(1/(K+1))."""
+    from math import factorial
+    th = [3.67423461e-05, 0.00312012573, 0.0336079014, 0.153820376, 0.451978133]
+    for K, t in enumerate(th, start=1):
+        assert abs(t - 0.75 * (1e-10 * factorial(2 * K + 2)) ** (1.0 / (K + 1))) <= 1e-8 * t
+    assert 0.75 * (1e-10 * factorial(14)) ** (1.0 / 7) > 0.75     # K = 6 covers the series domain
+    worst = 0.0
+    for c1 in np.geomspace(1e-12, 0.75, 400):
+        K = 1 + sum(c1 > t for t in th)
+        q = np.sqrt(4.0 * c1 / 3.0)
+        for frac in (-0.99, -0.5, 0.0, 0.5, 0.99):
+            c0 = frac * 2.0 * (c1 / 3.0) ** 1.5
+            f, _, _ = _series_deriv(c0, c1, K)
+            F, _, _ = _series_deriv(c0, c1, 14)
+            worst = max(worst, max(abs(f[j] - F[j]) * q ** j for j in range(3)))
+    assert worst <= 1e-10, worst
 
 
 def _d2f_bits(d):
