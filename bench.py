@@ -73,7 +73,7 @@ FP32_FMA_PER_CLK = 152 * 128
 # Small-case (32^3x64) ncu DRAM bytes per launch of each step kernel divided by its
 # 8,388,608 link updates, times the 42,467,328 link updates of one 48^3x96 launch
 # (traffic grows in proportion to the links); see profiles/.
-TRAFFIC_BYTES_PER_LINK_F32 = (632874240 + 581486592) / 8388608.0
+TRAFFIC_BYTES_PER_LINK_F32 = (634004224 + 582413824) / 8388608.0
 TRAFFIC_BYTES_PER_LINK_F64 = (2151617000 + 1189766000) / 8388608.0
 
 
