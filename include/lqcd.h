@@ -272,7 +272,7 @@ typedef struct lq_stout_opts {
  * The coefficients come from [MP] Sec. III's closed form, or, for
  * c1 = tr(Q^2)/2 <= 3/4, from the Taylor series of exp(iQ) reduced with
  * Q^3 = c1 Q + c0, truncated where its error bound is under 1e-17 (FP64
- * links) or 1e-13 (FP32 links).
+ * links) or 1e-10 (FP32 links, whose coefficients are rounded to FP32).
  * rho >= 0 and finite; n_steps >= 0; dirs_mask in [1, 15]. */
 lq_status lq_stout_smear(lq_field* links_inout, double rho, int n_steps, unsigned dirs_mask,
                          const lq_stout_opts* opts, void* stream);
