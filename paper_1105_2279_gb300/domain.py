@@ -136,6 +136,8 @@ def stout_backward(field, slab, rho, n_steps, dirs=(0, 1, 2, 3), force_out=None,
     steps at the link itself and needs no exchange."""
     if force_out is None and grad_out is None:
         raise ValueError("give force_out and/or grad_out")
+    if n_steps < 0:
+        raise ValueError("n_steps must be >= 0")
     s0, s1 = slab.interior
     U = [Field(field.geom, LQ_LINKS, field.prec)]
     U[0].tensor.copy_(field.tensor)

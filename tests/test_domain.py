@@ -95,3 +95,15 @@ def test_tslab_force_reproduces_the_oracle(world, dims, n, dirs, with_seed):
     G = np.concatenate([out[r][1] for r in range(world)], axis=0)
     assert np.max(np.abs(F - F_ref)) <= 1e-13 * np.max(np.abs(F_ref))
     assert np.max(np.abs(G - G_ref)) <= 1e-13 * np.max(np.abs(G_ref))
+
+
+def test_tslab_force_rejects_bad_arguments():
+    import types
+
+    from paper_1105_2279_gb300 import domain
+    slab = domain.TSlab((2, 2, 2, 4), 0, 1)
+    f = types.SimpleNamespace(geom=slab.local_dims, prec=None, tensor=None)
+    with pytest.raises(ValueError, match="force_out"):
+        domain.stout_backward(f, slab, 0.1, 1)
+    with pytest.raises(ValueError, match="n_steps"):
+        domain.stout_backward(f, slab, 0.1, -1, force_out=f)
